@@ -1,0 +1,217 @@
+/*
+ * stg.h -- C ABI of the GB300 staggered-fermion Dirac operator and CG solver.
+ *
+ * The operation (Jang, Kim, Lee, Lattice 2011, "Multi GPU Performance of
+ * Conjugate Gradient Solver with Staggered Fermions in Mixed Precision"):
+ *
+ *   Dirac operator (Eq. 4/5), with the staggered phase folded into the links
+ *   as in the paper's gauge-link preconditioning step (Sec. 2):
+ *     (D chi)(x) = sum_mu s_mu(x) U_mu(x) chi(x+mu)
+ *                       - s_mu(x-mu) U_mu(x-mu)^dag chi(x-mu),
+ *     s_mu(x) = eta_mu(x) b_mu(x),  eta_mu(x) = (-1)^(x_0+...+x_{mu-1})
+ *     (mu = x, y, z, t), b_t(x) = -1 on the last time slice (antiperiodic
+ *     time boundary), +1 otherwise.  There is no factor 1/2 in D.
+ *   Normal operator (Eq. 2/3) on even sites:  A = m^2 - D_eo D_oe.
+ *   Linear system (Eq. 1):  b = A x, solved by CG (Fig. 1) or by mixed-
+ *   precision CG (Fig. 2) with the corrected inner start of Eq. 6 and the
+ *   reliable / group-wise updates of Sec. 3.2.
+ *
+ * Conventions shared by every entry point:
+ *
+ *   Lattice.  dims = {Lx, Ly, Lz, Lt}, every extent even and >= 2 (else
+ *   STG_ERR_DIMS).  V = Lx Ly Lz Lt, Vh = V / 2.  Site x = (x, y, z, t) has
+ *   lexicographic index lex = x + Lx (y + Ly (z + Lz t)), parity
+ *   (x + y + z + t) & 1 (0 = even) and checkerboard index i = lex >> 1.
+ *
+ *   Canonical layouts (what callers hand over):
+ *     links:  complex128 [Lt][Lz][Ly][Lx][4][3][3] row-major U_mu(x)[a][b],
+ *             *without* phases or boundary signs (host memory);
+ *     fields: complex128 [Vh][3] over one parity in checkerboard order
+ *             (device memory), i.e. 6 doubles (re, im) x 3 colours per site.
+ *   Device layouts ("field" arguments below) are the library's structure-of-
+ *   arrays forms for FP64 / FP32 / FP16; stg_field_bytes() gives their size
+ *   and stg_pack_field() / stg_unpack_field() convert.
+ *
+ *   Ownership.  The caller owns every buffer it passes; the library never
+ *   frees or retains caller pointers beyond the call.  The library owns the
+ *   gauge handle's device copies of the links and a per-handle workspace
+ *   (allocated on first use, freed by stg_gauge_destroy).  Calls that use the
+ *   same handle must not overlap (one host thread and one stream at a time);
+ *   distinct handles are independent.
+ *
+ *   Streams.  Every call enqueues its GPU work on `stream` (NULL = the legacy
+ *   default stream).  stg_dslash, stg_apply_A*, stg_pack_field and
+ *   stg_unpack_field return once work is enqueued; stg_gauge_create and
+ *   stg_cg_solve return after their results are complete.
+ *
+ *   Errors.  Functions never abort and never print.  They return a status;
+ *   stg_last_error() gives a per-thread text for the most recent failure
+ *   (including the CUDA error string for STG_ERR_CUDA).  Invalid pointers
+ *   that are non-NULL cannot be detected: device pointers must point to at
+ *   least the stated number of bytes on the current device, 16-byte aligned.
+ */
+#ifndef STG_H
+#define STG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t; NULL selects the legacy default stream. */
+typedef struct CUstream_st *stg_stream_t;
+
+typedef enum stg_status {
+    STG_OK = 0,
+    STG_ERR_INVALID_ARG = 1,   /* NULL pointer, bad enum, bad size, NaN input */
+    STG_ERR_DIMS = 2,          /* a lattice extent is odd, zero or negative   */
+    STG_ERR_OOM = 3,           /* device or host allocation failed            */
+    STG_ERR_CUDA = 4,          /* a CUDA runtime call failed                  */
+    STG_ERR_NOT_CONVERGED = 5, /* maxiter reached; stats and x still filled   */
+    STG_ERR_BREAKDOWN = 6,     /* d^dag A d <= 0 or a non-finite reduction     */
+    STG_ERR_TIMEOUT = 7,       /* a bounded device-side wait gave up           */
+    STG_ERR_UNSUPPORTED = 8    /* precision / reconstruction not held by handle */
+} stg_status;
+
+typedef enum stg_prec { STG_FP64 = 0, STG_FP32 = 1, STG_FP16 = 2 } stg_prec;
+
+typedef enum stg_cg_policy {
+    STG_CG_RELIABLE = 0, /* Sec. 3.2: Eq. 6 start, reliable + group-wise update */
+    STG_CG_REFINE = 1,   /* Fig. 2: plain iterative refinement, d restarted    */
+    STG_CG_PLAIN = 2     /* Fig. 1 in FP64 only (sloppy precision ignored)     */
+} stg_cg_policy;
+
+typedef struct stg_cg_params {
+    int policy;        /* stg_cg_policy                                        */
+    int sloppy;        /* stg_prec of the inner iterations; must be FP64 or the
+                          handle's sloppy precision                            */
+    double delta;      /* eps^in of Sec. 3.2: an update fires when
+                          |r^y| < delta * max|r^y| since the last update       */
+    long maxiter;      /* bound on the total iteration count (0 = 10 N_dim,
+                          N_dim = 3 Vh as in Fig. 1)                           */
+    int check_every;   /* inner iterations between host checks (0 = auto)     */
+} stg_cg_params;
+
+typedef struct stg_cg_stats {
+    long iters;            /* iterations, all precisions                        */
+    long sloppy_iters;     /* of which in the sloppy (inner) precision          */
+    long updates;          /* FP64 true-residual recomputations (Sec. 3.2)     */
+    double true_res;       /* |b - A x| / |b| with the FP64 operator at exit   */
+    double iter_res;       /* iterated residual / |b| at exit                  */
+    double seconds;        /* wall time of the solve (host clock)              */
+} stg_cg_stats;
+
+typedef struct stg_gauge stg_gauge; /* opaque */
+
+/* Library version (monotone integer). */
+int stg_version(void);
+
+/* Static text for a status code. */
+const char *stg_status_string(stg_status s);
+
+/* Per-thread text describing the most recent failing call on this thread. */
+const char *stg_last_error(void);
+
+/*
+ * Build a gauge handle on the current CUDA device.
+ *   dims[4]     : Lx, Ly, Lz, Lt (even, >= 2).
+ *   links_host  : host complex128 [Lt][Lz][Ly][Lx][4][3][3] (canonical, no
+ *                 phases), 4 V 9 complex values; read during the call only.
+ *   sloppy      : low precision also held besides FP64 (STG_FP64 = none).
+ *   recon       : 18 (all 9 complex entries stored) or 12 (rows 0 and 1
+ *                 stored; row 2 rebuilt in the kernel as s conj(r0 x r1),
+ *                 which requires every U_mu(x) to be in SU(3); Sec. 3.3
+ *                 link compression).  Applies to the sloppy copy; the FP64
+ *                 copy uses recon only when sloppy == STG_FP64, else 18.
+ *   stream      : stream for the upload and packing (the call synchronises).
+ *   out         : receives the handle.
+ * Applies s_mu(x) once at pack time (the paper's link preconditioning).
+ * Errors: STG_ERR_DIMS, STG_ERR_INVALID_ARG (NULL, bad recon / precision),
+ * STG_ERR_OOM, STG_ERR_CUDA.
+ */
+stg_status stg_gauge_create(const int dims[4], const double *links_host,
+                            stg_prec sloppy, int recon, stg_stream_t stream,
+                            stg_gauge **out);
+
+/* Free the handle, its device links and its workspace.  NULL is a no-op. */
+stg_status stg_gauge_destroy(stg_gauge *g);
+
+/* Lattice extents and Vh of a handle. */
+stg_status stg_gauge_dims(const stg_gauge *g, int dims[4], long *vh);
+
+/*
+ * Bytes of one checkerboard field (Vh sites, 3 colours) in the device layout
+ * of `prec`: FP64 48 Vh (three double2 planes), FP32 24 Vh (float4 plane for
+ * colours 0-1, float2 plane for colour 2), FP16 16 Vh (per site three half2
+ * colours and one float scale in one 16-byte record).
+ */
+stg_status stg_field_bytes(const stg_gauge *g, stg_prec prec, size_t *bytes);
+
+/*
+ * Convert a canonical complex128 [Vh][3] device field to / from the device
+ * layout of `prec` (rounding to nearest on the way down; FP16 stores each
+ * site's colour vector divided by its largest |re| or |im| plus that scale).
+ * Buffers must not overlap.
+ */
+stg_status stg_pack_field(const stg_gauge *g, stg_prec prec, const double *canon_dev,
+                          void *field_dev, stg_stream_t stream);
+stg_status stg_unpack_field(const stg_gauge *g, stg_prec prec, const void *field_dev,
+                            double *canon_dev, stg_stream_t stream);
+
+/*
+ * One Dslash half-pass (Eq. 5): out = D_{p <- 1-p} in, with p = out_parity.
+ *   in_dev  : field of parity 1-p in the device layout of prec;
+ *   out_dev : field of parity p, same layout; must not alias in_dev.
+ *   prec    : STG_FP64, or the handle's sloppy precision.
+ * Errors: STG_ERR_INVALID_ARG, STG_ERR_UNSUPPORTED, STG_ERR_CUDA.
+ */
+stg_status stg_dslash(const stg_gauge *g, int out_parity, const void *in_dev,
+                      void *out_dev, stg_prec prec, stg_stream_t stream);
+
+/*
+ * Even-site normal operator (Eq. 3): out = m^2 in - D_eo (D_oe in).
+ * in_dev / out_dev: even fields in the device layout of prec (no aliasing).
+ * The odd intermediate lives in the handle's workspace.
+ */
+stg_status stg_apply_A(const stg_gauge *g, double mass, const void *in_dev,
+                       void *out_dev, stg_prec prec, stg_stream_t stream);
+
+/*
+ * Same as stg_apply_A and, fused into the second half-pass, the CG
+ * denominator d^dag A d = Re sum_x in(x)^dag out(x) accumulated in FP64
+ * (Sec. 3.2: all inner products in double).  dot_dev: one device double,
+ * written when the work completes; the summation order is fixed, so the
+ * value is bitwise reproducible for a given lattice and precision.
+ */
+stg_status stg_apply_A_dot(const stg_gauge *g, double mass, const void *in_dev,
+                           void *out_dev, double *dot_dev, stg_prec prec,
+                           stg_stream_t stream);
+
+/* Fill params with the defaults: RELIABLE, sloppy = handle's sloppy
+ * precision, delta = 0.1, maxiter = 0 (10 N_dim), check_every = 0 (auto). */
+stg_status stg_cg_params_default(const stg_gauge *g, stg_cg_params *params);
+
+/*
+ * Solve A x = b on even sites (Eq. 1, A of Eq. 3).
+ *   src_dev : canonical complex128 [Vh][3] device field b.
+ *   x_dev   : canonical complex128 [Vh][3] device field; on entry the
+ *             initial guess x0 (zeros for the paper's start), on exit x.
+ *   mass    : m >= 0; tol > 0: stop when |b - A x| <= tol |b| with the FP64
+ *             operator (the relative form of Fig. 1 / Fig. 2).
+ *   params  : NULL = stg_cg_params_default.
+ *   stats   : may be NULL.
+ * Returns STG_OK on convergence, STG_ERR_NOT_CONVERGED after maxiter (x
+ * holds the last iterate, stats filled), STG_ERR_BREAKDOWN, STG_ERR_INVALID_ARG
+ * (NULL, non-finite b / mass / tol), or a CUDA / OOM error.  Synchronises
+ * `stream` before returning.
+ */
+stg_status stg_cg_solve(const stg_gauge *g, const double *src_dev, double *x_dev,
+                        double mass, double tol, const stg_cg_params *params,
+                        stg_cg_stats *stats, stg_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STG_H */

@@ -1,0 +1,210 @@
+"""GB300 staggered-fermion Dirac operator and CG solver (Python binding).
+
+A thin ctypes layer over the C ABI of ``include/stg.h``: every function
+below has the name of the C entry point it calls and only marshals
+arguments (device pointers, sizes, the CUDA stream).  All arithmetic runs in
+the CUDA library ``libstg.so``; there is no Python or CPU fallback, and
+importing this package fails loudly when the library has not been built
+(``python -m paper_1111_0125_gb300.build`` or ``__graft_entry__.build()``).
+
+PyTorch is used only as plumbing: tensors for device memory and the current
+CUDA stream.  Pointer arguments accept an ``int`` address or a tensor.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libstg.so")
+
+STG_FP64, STG_FP32, STG_FP16 = 0, 1, 2
+STG_CG_RELIABLE, STG_CG_REFINE, STG_CG_PLAIN = 0, 1, 2
+(STG_OK, STG_ERR_INVALID_ARG, STG_ERR_DIMS, STG_ERR_OOM, STG_ERR_CUDA,
+ STG_ERR_NOT_CONVERGED, STG_ERR_BREAKDOWN, STG_ERR_TIMEOUT,
+ STG_ERR_UNSUPPORTED) = range(9)
+
+PREC_NAMES = {STG_FP64: "f64", STG_FP32: "f32", STG_FP16: "f16"}
+FIELD_SITE_BYTES = {STG_FP64: 48, STG_FP32: 24, STG_FP16: 16}
+
+
+class StgError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str, stats=None):
+        self.status = status
+        self.stats = stats
+        super().__init__(f"{where}: {_STATUS.get(status, status)}: {detail}")
+
+
+_STATUS = {STG_OK: "ok", STG_ERR_INVALID_ARG: "invalid argument",
+           STG_ERR_DIMS: "invalid lattice dimensions", STG_ERR_OOM: "out of memory",
+           STG_ERR_CUDA: "CUDA error", STG_ERR_NOT_CONVERGED: "not converged",
+           STG_ERR_BREAKDOWN: "CG breakdown", STG_ERR_TIMEOUT: "device wait timed out",
+           STG_ERR_UNSUPPORTED: "unsupported precision or reconstruction"}
+
+
+class stg_cg_params(ctypes.Structure):
+    _fields_ = [("policy", ctypes.c_int), ("sloppy", ctypes.c_int),
+                ("delta", ctypes.c_double), ("maxiter", ctypes.c_long),
+                ("check_every", ctypes.c_int)]
+
+
+class stg_cg_stats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_long), ("sloppy_iters", ctypes.c_long),
+                ("updates", ctypes.c_long), ("true_res", ctypes.c_double),
+                ("iter_res", ctypes.c_double), ("seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(
+            f"{LIB_PATH} is missing: the CUDA library has not been built "
+            "(run `python -m paper_1111_0125_gb300.build`); there is no fallback")
+    lib = ctypes.CDLL(LIB_PATH)
+    p, i, d, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+    sig = {
+        "stg_version": (i, []),
+        "stg_status_string": (ctypes.c_char_p, [i]),
+        "stg_last_error": (ctypes.c_char_p, []),
+        "stg_gauge_create": (i, [p, p, i, i, p, p]),
+        "stg_gauge_destroy": (i, [p]),
+        "stg_gauge_dims": (i, [p, p, p]),
+        "stg_field_bytes": (i, [p, i, p]),
+        "stg_pack_field": (i, [p, i, p, p, p]),
+        "stg_unpack_field": (i, [p, i, p, p, p]),
+        "stg_dslash": (i, [p, i, p, p, i, p]),
+        "stg_apply_A": (i, [p, d, p, p, i, p]),
+        "stg_apply_A_dot": (i, [p, d, p, p, p, i, p]),
+        "stg_cg_params_default": (i, [p, p]),
+        "stg_cg_solve": (i, [p, p, p, d, d, p, p, p]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+def _ptr(x) -> int:
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return int(x.data_ptr())
+    if isinstance(x, np.ndarray):
+        return int(x.ctypes.data)
+    raise TypeError(f"cannot take a pointer of {type(x)}")
+
+
+def _stream(s) -> int:
+    if s is None:
+        import torch
+        return int(torch.cuda.current_stream().cuda_stream)
+    if isinstance(s, int):
+        return s
+    return int(s.cuda_stream)
+
+
+def _check(st: int, where: str, stats=None):
+    if st != STG_OK:
+        raise StgError(st, where, stg_last_error(), stats)
+
+
+def stg_version() -> int:
+    return lib.stg_version()
+
+
+def stg_status_string(status: int) -> str:
+    return lib.stg_status_string(status).decode()
+
+
+def stg_last_error() -> str:
+    return lib.stg_last_error().decode()
+
+
+def stg_gauge_create(dims, links_host: np.ndarray, sloppy: int = STG_FP32, recon: int = 18,
+                     stream=None) -> int:
+    """Upload canonical complex128 links [Lt][Lz][Ly][Lx][4][3][3] (host)."""
+    dd = np.ascontiguousarray(np.asarray(dims, dtype=np.int32).reshape(4))
+    links = np.ascontiguousarray(links_host, dtype=np.complex128)
+    lx, ly, lz, lt = (int(v) for v in dd)
+    if links.size != lx * ly * lz * lt * 4 * 9:
+        raise StgError(STG_ERR_INVALID_ARG, "stg_gauge_create",
+                       f"links have {links.size} entries, expected {lx * ly * lz * lt * 36}")
+    h = ctypes.c_void_p()
+    st = lib.stg_gauge_create(dd.ctypes.data, links.ctypes.data, int(sloppy), int(recon),
+                              _stream(stream), ctypes.byref(h))
+    _check(st, "stg_gauge_create")
+    return h.value
+
+
+def stg_gauge_destroy(handle: int) -> None:
+    lib.stg_gauge_destroy(handle)
+
+
+def stg_gauge_dims(handle: int):
+    dd = (ctypes.c_int * 4)()
+    vh = ctypes.c_long()
+    _check(lib.stg_gauge_dims(handle, dd, ctypes.byref(vh)), "stg_gauge_dims")
+    return tuple(dd), vh.value
+
+
+def stg_field_bytes(handle: int, prec: int) -> int:
+    n = ctypes.c_size_t()
+    _check(lib.stg_field_bytes(handle, int(prec), ctypes.byref(n)), "stg_field_bytes")
+    return n.value
+
+
+def stg_pack_field(handle: int, prec: int, canon_dev, field_dev, stream=None) -> None:
+    _check(lib.stg_pack_field(handle, int(prec), _ptr(canon_dev), _ptr(field_dev), _stream(stream)),
+           "stg_pack_field")
+
+
+def stg_unpack_field(handle: int, prec: int, field_dev, canon_dev, stream=None) -> None:
+    _check(lib.stg_unpack_field(handle, int(prec), _ptr(field_dev), _ptr(canon_dev), _stream(stream)),
+           "stg_unpack_field")
+
+
+def stg_dslash(handle: int, out_parity: int, in_dev, out_dev, prec: int, stream=None) -> None:
+    _check(lib.stg_dslash(handle, int(out_parity), _ptr(in_dev), _ptr(out_dev), int(prec),
+                          _stream(stream)), "stg_dslash")
+
+
+def stg_apply_A(handle: int, mass: float, in_dev, out_dev, prec: int, stream=None) -> None:
+    _check(lib.stg_apply_A(handle, float(mass), _ptr(in_dev), _ptr(out_dev), int(prec),
+                           _stream(stream)), "stg_apply_A")
+
+
+def stg_apply_A_dot(handle: int, mass: float, in_dev, out_dev, dot_dev, prec: int,
+                    stream=None) -> None:
+    _check(lib.stg_apply_A_dot(handle, float(mass), _ptr(in_dev), _ptr(out_dev), _ptr(dot_dev),
+                               int(prec), _stream(stream)), "stg_apply_A_dot")
+
+
+def stg_cg_params_default(handle: int) -> stg_cg_params:
+    p = stg_cg_params()
+    _check(lib.stg_cg_params_default(handle, ctypes.byref(p)), "stg_cg_params_default")
+    return p
+
+
+def stg_cg_solve(handle: int, src_dev, x_dev, mass: float, tol: float, params=None,
+                 stream=None) -> dict:
+    """Solve A x = b; x_dev holds x0 on entry.  Returns the stats as a dict;
+    raises StgError (with .stats) on any non-OK status."""
+    stats = stg_cg_stats()
+    pp = ctypes.byref(params) if params is not None else None
+    st = lib.stg_cg_solve(handle, _ptr(src_dev), _ptr(x_dev), float(mass), float(tol), pp,
+                          ctypes.byref(stats), _stream(stream))
+    _check(st, "stg_cg_solve", stats.as_dict())
+    return stats.as_dict()
+
+
+from .fields import Gauge  # noqa: E402  (convenience layer over the names above)

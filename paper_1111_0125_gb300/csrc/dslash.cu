@@ -1,0 +1,166 @@
+// Staggered Dslash half-pass (Eq. 5) and its fused epilogues.
+//
+// One thread per output site of parity p.  Per site the kernel reads the
+// four forward links U_mu(x) (parity p block, index i), the four backward
+// links U_mu(x - mu) (parity 1-p block, at the neighbour's index), and the
+// eight neighbour colour vectors of parity 1-p, then writes one colour
+// vector.  Every link is read exactly once per half-pass; each neighbour
+// vector is shared by eight sites and is served from L1/L2 after its first
+// read, so the compulsory HBM traffic is 8 links + 1 input + 1 output per
+// site.  The work is bandwidth-bound (0.36 flop/byte in FP64, 0.9 in
+// FP32/12), so there are no tensor cores here: the 3x3 complex mat-vecs run
+// on the FP32 / FP64 pipes in registers.
+//
+// Epilogues (all fused into the second half-pass of A, Eq. 3):
+//   EPI_NONE  out = D in
+//   EPI_GATE  out = D in, skipped when the CG state flag is raised
+//   EPI_A     out = m^2 w - D in                     (w = the even input d)
+//   EPI_A_DOT as EPI_A, plus Re sum w^dag out in FP64 -> *dot
+//   EPI_A_CG  as EPI_A_DOT inside CG: alpha = delta / d^dag A d -> state
+//   EPI_RES   out = w - m^2 v + D in = b - A x, plus |out|^2 in FP64 -> *dot
+#include "stg_internal.h"
+
+namespace stg {
+
+struct DslashArgs {
+    Geom g;
+    const char *lf[4];  // forward link blocks  (parity p,   mu)
+    const char *lb[4];  // backward link blocks (parity 1-p, mu)
+    int parity;
+    const void *in;
+    void *out;
+    const void *w;
+    const void *v;
+    double m2;
+    double *dot;
+    CGState *state;
+    double *partials;
+    unsigned *counter;
+};
+
+template <int P, int R, int EPI>
+__global__ void __launch_bounds__(kBlock) k_dslash(const DslashArgs a)
+{
+    typedef typename Real<P>::T T;
+    if (EPI == EPI_A_CG || EPI == EPI_GATE) {
+        if (a.state->flag != FLAG_RUN) return;  // uniform over the grid
+    }
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    const int vh = a.g.Vh;
+    double dot = 0.0;
+    if (i < vh) {
+        const Site s = site_of(a.g, i, a.parity);
+        Vec3<T> acc;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) acc.r[c] = acc.i[c] = T(0);
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) {
+            int jf, jb;
+            neighbours(a.g, s, i, mu, jf, jb);
+            float sf = 1.f, sb = 1.f;
+            if (R == 12) link_signs(a.g, s, mu, sf, sb);
+            const Mat3<T> uf = LinkIO<P, R>::load(a.lf[mu], vh, i, T(sf));
+            const Vec3<T> vf = FieldIO<P>::load_nc(a.in, vh, jf);
+            mul_add(uf, vf, acc);
+            const Mat3<T> ub = LinkIO<P, R>::load(a.lb[mu], vh, jb, T(sb));
+            const Vec3<T> vb = FieldIO<P>::load_nc(a.in, vh, jb);
+            adj_mul_sub(ub, vb, acc);
+        }
+        if (EPI == EPI_NONE || EPI == EPI_GATE) {
+            FieldIO<P>::store(a.out, vh, i, acc);
+        } else if (EPI == EPI_RES) {
+            const Vec3<T> b = FieldIO<P>::load_nc(a.w, vh, i);
+            const Vec3<T> x = FieldIO<P>::load_nc(a.v, vh, i);
+            const T m2 = T(a.m2);
+            Vec3<T> o;
+            T nr = T(0);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                o.r[c] = b.r[c] - m2 * x.r[c] + acc.r[c];
+                o.i[c] = b.i[c] - m2 * x.i[c] + acc.i[c];
+                nr += o.r[c] * o.r[c] + o.i[c] * o.i[c];
+            }
+            FieldIO<P>::store(a.out, vh, i, o);
+            dot = double(nr);
+        } else {
+            const T m2 = (EPI == EPI_A_CG) ? T(a.state->m2) : T(a.m2);
+            const Vec3<T> d = FieldIO<P>::load_nc(a.w, vh, i);
+            Vec3<T> o;
+            T dq = T(0);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                o.r[c] = m2 * d.r[c] - acc.r[c];
+                o.i[c] = m2 * d.i[c] - acc.i[c];
+                dq += d.r[c] * o.r[c] + d.i[c] * o.i[c];
+            }
+            FieldIO<P>::store(a.out, vh, i, o);
+            dot = double(dq);
+        }
+    }
+    if (EPI == EPI_A_DOT || EPI == EPI_A_CG || EPI == EPI_RES) {
+        double total;
+        if (grid_sum<kBlock>(dot, a.partials, a.counter, total)) {
+            if (EPI == EPI_A_CG) {
+                CGState *st = a.state;
+                st->pAp = total;
+                if (!(total > 0.0) || !isfinite(total)) st->flag = FLAG_BREAKDOWN;
+                else st->alpha = st->delta_new / total;
+            } else {
+                *a.dot = total;
+            }
+        }
+    }
+}
+
+template <int P, int R>
+static void launch_pr(int epi, const DslashArgs &a, int grid, cudaStream_t s)
+{
+    switch (epi) {
+    case EPI_NONE: k_dslash<P, R, EPI_NONE><<<grid, kBlock, 0, s>>>(a); break;
+    case EPI_A: k_dslash<P, R, EPI_A><<<grid, kBlock, 0, s>>>(a); break;
+    case EPI_A_DOT: k_dslash<P, R, EPI_A_DOT><<<grid, kBlock, 0, s>>>(a); break;
+    case EPI_A_CG: k_dslash<P, R, EPI_A_CG><<<grid, kBlock, 0, s>>>(a); break;
+    case EPI_RES: k_dslash<P, R, EPI_RES><<<grid, kBlock, 0, s>>>(a); break;
+    case EPI_GATE: k_dslash<P, R, EPI_GATE><<<grid, kBlock, 0, s>>>(a); break;
+    }
+}
+
+stg_status launch_dslash(const Geom &g, int prec, int epi, const DslashLaunch &L, cudaStream_t s)
+{
+    DslashArgs a;
+    a.g = g;
+    a.parity = L.out_parity;
+    for (int mu = 0; mu < 4; ++mu) {
+        a.lf[mu] = L.links->blk(L.out_parity, mu);
+        a.lb[mu] = L.links->blk(1 - L.out_parity, mu);
+    }
+    a.in = L.in;
+    a.out = L.out;
+    a.w = L.w;
+    a.v = L.v;
+    a.m2 = L.m2;
+    a.dot = L.dot;
+    a.state = L.state;
+    a.partials = L.partials;
+    a.counter = L.counter;
+    const int grid = (g.Vh + kBlock - 1) / kBlock;
+    const int recon = L.links->recon;
+    if (prec != L.links->prec) {
+        set_error("dslash: link precision does not match the field precision");
+        return STG_ERR_UNSUPPORTED;
+    }
+    if (prec == P64) {
+        if (recon == 18) launch_pr<P64, 18>(epi, a, grid, s);
+        else launch_pr<P64, 12>(epi, a, grid, s);
+    } else if (prec == P32) {
+        if (recon == 18) launch_pr<P32, 18>(epi, a, grid, s);
+        else launch_pr<P32, 12>(epi, a, grid, s);
+    } else {
+        if (recon == 18) launch_pr<P16, 18>(epi, a, grid, s);
+        else launch_pr<P16, 12>(epi, a, grid, s);
+    }
+    STG_CUDA(cudaGetLastError());
+    return STG_OK;
+}
+
+}  // namespace stg

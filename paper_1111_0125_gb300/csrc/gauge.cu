@@ -1,0 +1,300 @@
+// Gauge handle: upload of the canonical links, the paper's link
+// preconditioning (staggered phase and time-boundary sign folded into each
+// link, Sec. 2 after Eq. 5), re-layout into per-(parity, mu) structure-of-
+// arrays planes for coalesced 128-bit loads (the paper's host-side
+// "rearranging data for the coalesced access", Sec. 3.3, done here on the
+// GPU), and conversion of fields between the canonical and device layouts.
+#include <stdio.h>
+#include <stdlib.h>
+
+#include <new>
+
+#include "stg_internal.h"
+
+namespace stg {
+
+static size_t align256(size_t n) { return (n + 255) & ~(size_t)255; }
+
+Geom make_geom(const int dims[4])
+{
+    Geom g;
+    for (int mu = 0; mu < 4; ++mu) g.L[mu] = dims[mu];
+    g.Lxh = dims[0] / 2;
+    g.Vh = (int)((long)dims[0] * dims[1] * dims[2] * dims[3] / 2);
+    g.sy = g.Lxh;
+    g.sz = g.Lxh * dims[1];
+    g.st = g.Lxh * dims[1] * dims[2];
+    return g;
+}
+
+// ---------------------------------------------------------------------------
+// link packing: one thread per (site, mu) of the canonical array
+// ---------------------------------------------------------------------------
+template <int P, int R>
+__global__ void k_pack_links(Geom g, const double2 *__restrict__ ucan, char *base, size_t blk_bytes)
+{
+    const long n = (long)g.Vh * 2 * 4;
+    const long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int mu = (int)(k & 3);
+    const int lex = (int)(k >> 2);
+    int r = lex;
+    const int x = r % g.L[0]; r /= g.L[0];
+    const int y = r % g.L[1]; r /= g.L[1];
+    const int z = r % g.L[2];
+    const int t = r / g.L[2];
+    const int parity = (x + y + z + t) & 1;
+    const int i = lex >> 1;
+    int e = 0;
+    if (mu >= 1) e += x;
+    if (mu >= 2) e += y;
+    if (mu >= 3) e += z;
+    double s = (e & 1) ? -1.0 : 1.0;
+    if (mu == 3 && t == g.L[3] - 1) s = -s;
+    const double2 *src = ucan + (size_t)k * 9;
+    double2 u[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        double2 v = src[q];
+        u[q] = make_double2(s * v.x, s * v.y);
+    }
+    char *blk = base + (size_t)(parity * 4 + mu) * blk_bytes;
+    const int vh = g.Vh;
+    if (P == P64) {
+        double2 *p = reinterpret_cast<double2 *>(blk);
+        const int ne = R == 18 ? 9 : 6;
+        for (int q = 0; q < ne; ++q) p[(size_t)q * vh + i] = u[q];
+    } else if (P == P32) {
+        float4 *p = reinterpret_cast<float4 *>(blk);
+        const int n4 = R == 18 ? 4 : 3;
+        for (int q = 0; q < n4; ++q)
+            p[(size_t)q * vh + i] = make_float4((float)u[2 * q].x, (float)u[2 * q].y,
+                                                (float)u[2 * q + 1].x, (float)u[2 * q + 1].y);
+        if (R == 18)
+            reinterpret_cast<float2 *>(p + (size_t)4 * vh)[i] = make_float2((float)u[8].x, (float)u[8].y);
+    } else {
+        uint4 *p = reinterpret_cast<uint4 *>(blk);
+        uint4 a;
+        a.x = f2_to_h2((float)u[0].x, (float)u[0].y);
+        a.y = f2_to_h2((float)u[1].x, (float)u[1].y);
+        a.z = f2_to_h2((float)u[2].x, (float)u[2].y);
+        a.w = f2_to_h2((float)u[3].x, (float)u[3].y);
+        p[i] = a;
+        if (R == 18) {
+            uint4 b;
+            b.x = f2_to_h2((float)u[4].x, (float)u[4].y);
+            b.y = f2_to_h2((float)u[5].x, (float)u[5].y);
+            b.z = f2_to_h2((float)u[6].x, (float)u[6].y);
+            b.w = f2_to_h2((float)u[7].x, (float)u[7].y);
+            p[(size_t)vh + i] = b;
+            reinterpret_cast<unsigned *>(p + (size_t)2 * vh)[i] = f2_to_h2((float)u[8].x, (float)u[8].y);
+        } else {
+            uint2 b;
+            b.x = f2_to_h2((float)u[4].x, (float)u[4].y);
+            b.y = f2_to_h2((float)u[5].x, (float)u[5].y);
+            reinterpret_cast<uint2 *>(p + (size_t)vh)[i] = b;
+        }
+    }
+}
+
+static stg_status pack_links(const Geom &g, const double2 *ucan, int prec, int recon,
+                             LinkField *lf, cudaStream_t s)
+{
+    lf->prec = prec;
+    lf->recon = recon;
+    lf->blk_bytes = align256((size_t)g.Vh * link_bytes(prec, recon));
+    cudaError_t e = cudaMalloc((void **)&lf->base, lf->blk_bytes * 8);
+    if (e != cudaSuccess) {
+        lf->base = nullptr;
+        set_error("stg_gauge_create: device allocation of the links failed");
+        return e == cudaErrorMemoryAllocation ? STG_ERR_OOM : cuda_fail(e, "cudaMalloc");
+    }
+    const long n = (long)g.Vh * 8;
+    const int grid = (int)((n + 255) / 256);
+#define STG_PACK(P_, R_) k_pack_links<P_, R_><<<grid, 256, 0, s>>>(g, ucan, lf->base, lf->blk_bytes)
+    if (prec == P64) { if (recon == 18) STG_PACK(P64, 18); else STG_PACK(P64, 12); }
+    else if (prec == P32) { if (recon == 18) STG_PACK(P32, 18); else STG_PACK(P32, 12); }
+    else { if (recon == 18) STG_PACK(P16, 18); else STG_PACK(P16, 12); }
+#undef STG_PACK
+    STG_CUDA(cudaGetLastError());
+    return STG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// field packing
+// ---------------------------------------------------------------------------
+template <int P>
+__global__ void k_pack_field(int vh, const double2 *__restrict__ canon, void *out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= vh) return;
+    typedef typename Real<P>::T T;
+    Vec3<T> v;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        double2 a = canon[(size_t)i * 3 + c];
+        v.r[c] = T(a.x);
+        v.i[c] = T(a.y);
+    }
+    FieldIO<P>::store(out, vh, i, v);
+}
+
+template <int P>
+__global__ void k_unpack_field(int vh, const void *in, double2 *__restrict__ canon)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= vh) return;
+    const auto v = FieldIO<P>::load(in, vh, i);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) canon[(size_t)i * 3 + c] = make_double2(double(v.r[c]), double(v.i[c]));
+}
+
+stg_status pack_field(const Geom &g, int prec, const double *canon, void *out, cudaStream_t s)
+{
+    const int grid = (g.Vh + 255) / 256;
+    const double2 *c = reinterpret_cast<const double2 *>(canon);
+    if (prec == P64) k_pack_field<P64><<<grid, 256, 0, s>>>(g.Vh, c, out);
+    else if (prec == P32) k_pack_field<P32><<<grid, 256, 0, s>>>(g.Vh, c, out);
+    else k_pack_field<P16><<<grid, 256, 0, s>>>(g.Vh, c, out);
+    STG_CUDA(cudaGetLastError());
+    return STG_OK;
+}
+
+stg_status unpack_field(const Geom &g, int prec, const void *in, double *canon, cudaStream_t s)
+{
+    const int grid = (g.Vh + 255) / 256;
+    double2 *c = reinterpret_cast<double2 *>(canon);
+    if (prec == P64) k_unpack_field<P64><<<grid, 256, 0, s>>>(g.Vh, in, c);
+    else if (prec == P32) k_unpack_field<P32><<<grid, 256, 0, s>>>(g.Vh, in, c);
+    else k_unpack_field<P16><<<grid, 256, 0, s>>>(g.Vh, in, c);
+    STG_CUDA(cudaGetLastError());
+    return STG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// handle
+// ---------------------------------------------------------------------------
+const LinkField *links_for(const stg_gauge *g, int prec)
+{
+    if (prec == P64) return &g->hi;
+    if (g->lo.base && g->lo.prec == prec) return &g->lo;
+    return nullptr;
+}
+
+stg_status gauge_create(const int dims[4], const double *links_host, int sloppy, int recon,
+                        cudaStream_t s, stg_gauge **out)
+{
+    stg_gauge *g = new (std::nothrow) stg_gauge();
+    if (!g) {
+        set_error("stg_gauge_create: host allocation failed");
+        return STG_ERR_OOM;
+    }
+    for (int mu = 0; mu < 4; ++mu) g->dims[mu] = dims[mu];
+    g->geom = make_geom(dims);
+    g->sloppy = sloppy;
+    g->ws = nullptr;
+    cudaError_t e = cudaGetDevice(&g->device);
+    if (e != cudaSuccess) {
+        delete g;
+        return cuda_fail(e, "cudaGetDevice");
+    }
+    const size_t canon_bytes = (size_t)g->geom.Vh * 2 * 4 * 9 * sizeof(double2);
+    double2 *ucan = nullptr;
+    stg_status st = STG_OK;
+    e = cudaMalloc((void **)&ucan, canon_bytes);
+    if (e != cudaSuccess) {
+        delete g;
+        set_error("stg_gauge_create: device staging allocation failed");
+        return e == cudaErrorMemoryAllocation ? STG_ERR_OOM : cuda_fail(e, "cudaMalloc");
+    }
+    e = cudaMemcpyAsync(ucan, links_host, canon_bytes, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) st = cuda_fail(e, "cudaMemcpyAsync(links)");
+    const int recon_hi = (sloppy == P64) ? recon : 18;
+    if (st == STG_OK) st = pack_links(g->geom, ucan, P64, recon_hi, &g->hi, s);
+    if (st == STG_OK && sloppy != P64) st = pack_links(g->geom, ucan, sloppy, recon, &g->lo, s);
+    e = cudaStreamSynchronize(s);
+    if (st == STG_OK && e != cudaSuccess) st = cuda_fail(e, "cudaStreamSynchronize");
+    cudaFree(ucan);
+    if (st != STG_OK) {
+        if (g->hi.base) cudaFree(g->hi.base);
+        if (g->lo.base) cudaFree(g->lo.base);
+        delete g;
+        return st;
+    }
+    *out = g;
+    return STG_OK;
+}
+
+void gauge_destroy(stg_gauge *g)
+{
+    if (!g) return;
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != g->device) cudaSetDevice(g->device);
+    if (g->ws) workspace_free(g->ws);
+    if (g->hi.base) cudaFree(g->hi.base);
+    if (g->lo.base) cudaFree(g->lo.base);
+    if (cur >= 0 && cur != g->device) cudaSetDevice(cur);
+    delete g;
+}
+
+// ---------------------------------------------------------------------------
+// workspace
+// ---------------------------------------------------------------------------
+stg_status workspace_get(stg_gauge *g, Workspace **out)
+{
+    if (g->ws) {
+        *out = g->ws;
+        return STG_OK;
+    }
+    Workspace *ws = new (std::nothrow) Workspace();
+    if (!ws) {
+        set_error("workspace: host allocation failed");
+        return STG_ERR_OOM;
+    }
+    ws->n_partials = (size_t)((g->geom.Vh + kBlock - 1) / kBlock) + 64;
+    cudaError_t e = cudaMalloc((void **)&ws->partials, ws->n_partials * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&ws->state, sizeof(CGState));
+    if (e == cudaSuccess) e = cudaMemset(ws->state, 0, sizeof(CGState));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&ws->state_host, sizeof(CGState));
+    if (e != cudaSuccess) {
+        workspace_free(ws);
+        set_error("workspace: allocation failed");
+        return e == cudaErrorMemoryAllocation ? STG_ERR_OOM : cuda_fail(e, "workspace");
+    }
+    g->ws = ws;
+    *out = ws;
+    return STG_OK;
+}
+
+stg_status workspace_tmp(stg_gauge *g, int prec, void **out)
+{
+    Workspace *ws;
+    STG_TRY(workspace_get(g, &ws));
+    if (!ws->tmp[prec]) {
+        size_t n = (size_t)g->geom.Vh * field_site_bytes(prec);
+        cudaError_t e = cudaMalloc(&ws->tmp[prec], n);
+        if (e != cudaSuccess) {
+            ws->tmp[prec] = nullptr;
+            set_error("workspace: allocation of the odd intermediate failed");
+            return e == cudaErrorMemoryAllocation ? STG_ERR_OOM : cuda_fail(e, "cudaMalloc");
+        }
+    }
+    *out = ws->tmp[prec];
+    return STG_OK;
+}
+
+void workspace_free(Workspace *ws)
+{
+    if (!ws) return;
+    if (ws->graph) cudaGraphExecDestroy(ws->graph);
+    cudaFree(ws->partials);
+    cudaFree(ws->state);
+    if (ws->state_host) cudaFreeHost(ws->state_host);
+    for (int p = 0; p < 3; ++p) cudaFree(ws->tmp[p]);
+    void *v[] = {ws->x64, ws->b64, ws->r64, ws->t64, ws->y, ws->r, ws->d, ws->q};
+    for (void *p : v) cudaFree(p);
+    delete ws;
+}
+
+}  // namespace stg

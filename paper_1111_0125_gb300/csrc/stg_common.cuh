@@ -1,0 +1,434 @@
+// Device-side building blocks shared by the library's kernels: lattice
+// geometry on the even/odd checkerboard, the structure-of-arrays field and
+// link layouts per precision, SU(3) algebra, and a deterministic FP64
+// grid reduction.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace stg {
+
+enum Prec { P64 = 0, P32 = 1, P16 = 2 };
+
+// ---------------------------------------------------------------------------
+// Geometry.  Site (x, y, z, t), lex = x + Lx (y + Ly (z + Lz t)), parity
+// (x+y+z+t) & 1, checkerboard index i = lex >> 1 (Lx even).  Within one
+// parity the y, z and t neighbours are at i +- sy, sz, st; the x neighbour
+// keeps the row (i - x/2) and moves x/2 by the parity-dependent hop.
+// ---------------------------------------------------------------------------
+struct Geom {
+    int L[4];  // Lx, Ly, Lz, Lt
+    int Lxh;   // Lx / 2
+    int Vh;    // sites per parity
+    int sy, sz, st;
+};
+
+struct Site {
+    int x, y, z, t;
+    int row;  // i - x/2, start of the x-row on the checkerboard
+};
+
+__device__ __forceinline__ Site site_of(const Geom &g, int i, int parity)
+{
+    Site s;
+    int xh = i % g.Lxh;
+    int r = i / g.Lxh;
+    s.row = i - xh;
+    s.y = r % g.L[1];
+    r /= g.L[1];
+    s.z = r % g.L[2];
+    s.t = r / g.L[2];
+    s.x = 2 * xh + ((parity + s.y + s.z + s.t) & 1);
+    return s;
+}
+
+// checkerboard index of x + mu (fwd) and x - mu (bwd) in the opposite parity
+__device__ __forceinline__ void neighbours(const Geom &g, const Site &s, int i, int mu,
+                                           int &jf, int &jb)
+{
+    if (mu == 0) {
+        int xf = (s.x + 1 == g.L[0]) ? 0 : s.x + 1;
+        int xb = (s.x == 0) ? g.L[0] - 1 : s.x - 1;
+        jf = s.row + (xf >> 1);
+        jb = s.row + (xb >> 1);
+    } else if (mu == 1) {
+        jf = (s.y == g.L[1] - 1) ? i - (g.L[1] - 1) * g.sy : i + g.sy;
+        jb = (s.y == 0) ? i + (g.L[1] - 1) * g.sy : i - g.sy;
+    } else if (mu == 2) {
+        jf = (s.z == g.L[2] - 1) ? i - (g.L[2] - 1) * g.sz : i + g.sz;
+        jb = (s.z == 0) ? i + (g.L[2] - 1) * g.sz : i - g.sz;
+    } else {
+        jf = (s.t == g.L[3] - 1) ? i - (g.L[3] - 1) * g.st : i + g.st;
+        jb = (s.t == 0) ? i + (g.L[3] - 1) * g.st : i - g.st;
+    }
+}
+
+// s_mu = eta_mu * b_mu for the link leaving x (fwd) and the link leaving
+// x - mu (bwd).  eta_mu(x - mu) = eta_mu(x) since eta_mu ignores x_mu.
+__device__ __forceinline__ void link_signs(const Geom &g, const Site &s, int mu,
+                                           float &sf, float &sb)
+{
+    int e = 0;
+    if (mu >= 1) e += s.x;
+    if (mu >= 2) e += s.y;
+    if (mu >= 3) e += s.z;
+    float eta = (e & 1) ? -1.f : 1.f;
+    sf = eta;
+    sb = eta;
+    if (mu == 3) {
+        if (s.t == g.L[3] - 1) sf = -sf;
+        if (s.t == 0) sb = -sb;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Precision traits
+// ---------------------------------------------------------------------------
+template <int P> struct Real { typedef float T; };
+template <> struct Real<P64> { typedef double T; };
+
+// Bytes per site of one checkerboard field in the device layout.
+__host__ __device__ constexpr int field_site_bytes(int p)
+{
+    return p == P64 ? 48 : (p == P32 ? 24 : 16);
+}
+
+// Bytes of one link in the device layout.
+__host__ __device__ constexpr int link_bytes(int p, int recon)
+{
+    return p == P64 ? (recon == 18 ? 144 : 96)
+         : p == P32 ? (recon == 18 ? 72 : 48)
+                    : (recon == 18 ? 36 : 24);
+}
+
+// ---------------------------------------------------------------------------
+// Colour vectors (3 complex) and their device layouts
+//   P64: three double2 planes [3][Vh]
+//   P32: float4 plane (c0, c1) then float2 plane (c2)
+//   P16: one 16-byte record per site {half2 c0, half2 c1, half2 c2, f32 scale}
+// ---------------------------------------------------------------------------
+template <typename T> struct Vec3 {
+    T r[3], i[3];
+};
+
+template <int P> struct FieldIO;
+
+// load_nc goes through the read-only data path and is only used for data
+// that no thread of the same kernel writes; load is a plain global load.
+template <typename V, bool NC> __device__ __forceinline__ V ld(const V *p)
+{
+    if (NC) return __ldg(p);
+    return *p;
+}
+
+template <> struct FieldIO<P64> {
+    template <bool NC = false>
+    __device__ __forceinline__ static Vec3<double> load(const void *f, int vh, int s)
+    {
+        const double2 *p = static_cast<const double2 *>(f);
+        Vec3<double> v;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            double2 a = ld<double2, NC>(p + (size_t)c * vh + s);
+            v.r[c] = a.x;
+            v.i[c] = a.y;
+        }
+        return v;
+    }
+    __device__ __forceinline__ static Vec3<double> load_nc(const void *f, int vh, int s)
+    {
+        return load<true>(f, vh, s);
+    }
+    __device__ __forceinline__ static void store(void *f, int vh, int s, const Vec3<double> &v)
+    {
+        double2 *p = static_cast<double2 *>(f);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) p[(size_t)c * vh + s] = make_double2(v.r[c], v.i[c]);
+    }
+};
+
+template <> struct FieldIO<P32> {
+    template <bool NC = false>
+    __device__ __forceinline__ static Vec3<float> load(const void *f, int vh, int s)
+    {
+        const float4 *p4 = static_cast<const float4 *>(f);
+        const float2 *p2 = reinterpret_cast<const float2 *>(p4 + vh);
+        float4 a = ld<float4, NC>(p4 + s);
+        float2 b = ld<float2, NC>(p2 + s);
+        Vec3<float> v;
+        v.r[0] = a.x; v.i[0] = a.y;
+        v.r[1] = a.z; v.i[1] = a.w;
+        v.r[2] = b.x; v.i[2] = b.y;
+        return v;
+    }
+    __device__ __forceinline__ static Vec3<float> load_nc(const void *f, int vh, int s)
+    {
+        return load<true>(f, vh, s);
+    }
+    __device__ __forceinline__ static void store(void *f, int vh, int s, const Vec3<float> &v)
+    {
+        float4 *p4 = static_cast<float4 *>(f);
+        float2 *p2 = reinterpret_cast<float2 *>(p4 + vh);
+        p4[s] = make_float4(v.r[0], v.i[0], v.r[1], v.i[1]);
+        p2[s] = make_float2(v.r[2], v.i[2]);
+    }
+};
+
+__device__ __forceinline__ float2 h2_to_f2(unsigned u)
+{
+    __half2 h = *reinterpret_cast<__half2 *>(&u);
+    return __half22float2(h);
+}
+
+__device__ __forceinline__ unsigned f2_to_h2(float a, float b)
+{
+    __half2 h = __floats2half2_rn(a, b);
+    return *reinterpret_cast<unsigned *>(&h);
+}
+
+template <> struct FieldIO<P16> {
+    template <bool NC = false>
+    __device__ __forceinline__ static Vec3<float> load(const void *f, int vh, int s)
+    {
+        uint4 u = ld<uint4, NC>(static_cast<const uint4 *>(f) + s);
+        float sc = __uint_as_float(u.w);
+        float2 a = h2_to_f2(u.x), b = h2_to_f2(u.y), c = h2_to_f2(u.z);
+        Vec3<float> v;
+        v.r[0] = a.x * sc; v.i[0] = a.y * sc;
+        v.r[1] = b.x * sc; v.i[1] = b.y * sc;
+        v.r[2] = c.x * sc; v.i[2] = c.y * sc;
+        return v;
+    }
+    __device__ __forceinline__ static Vec3<float> load_nc(const void *f, int vh, int s)
+    {
+        return load<true>(f, vh, s);
+    }
+    __device__ __forceinline__ static void store(void *f, int vh, int s, const Vec3<float> &v)
+    {
+        float m = 0.f;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) m = fmaxf(m, fmaxf(fabsf(v.r[c]), fabsf(v.i[c])));
+        float inv = m > 0.f ? 1.0f / m : 0.f;
+        uint4 u;
+        u.x = f2_to_h2(v.r[0] * inv, v.i[0] * inv);
+        u.y = f2_to_h2(v.r[1] * inv, v.i[1] * inv);
+        u.z = f2_to_h2(v.r[2] * inv, v.i[2] * inv);
+        u.w = __float_as_uint(m);
+        static_cast<uint4 *>(f)[s] = u;
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Links.  One block per (parity, mu) holding Vh links as planes:
+//   P64/18: 9 double2 planes (entries 00..22);  P64/12: 6 (rows 0, 1)
+//   P32/18: 4 float4 planes (00,01)(02,10)(11,12)(20,21) + float2 plane 22
+//   P32/12: 3 float4 planes (00,01)(02,10)(11,12)
+//   P16/18: 2 uint4 planes of 4 half2 + one 4-byte half2 plane (22)
+//   P16/12: 1 uint4 plane (00,01,02,10) + one uint2 plane (11,12)
+// For recon 12 row 2 = s * conj(row0 x row1), s = the folded phase of the
+// link (s U is stored; det(s U) = s for U in SU(3)).
+// ---------------------------------------------------------------------------
+template <typename T> struct Mat3 {
+    T r[3][3], i[3][3];
+};
+
+template <typename T>
+__device__ __forceinline__ void set_entry(Mat3<T> &u, int k, T re, T im)
+{
+    u.r[k / 3][k % 3] = re;
+    u.i[k / 3][k % 3] = im;
+}
+
+template <typename T>
+__device__ __forceinline__ void reconstruct_row2(Mat3<T> &u, T s)
+{
+    // (r0 x r1)_a = r0_{a+1} r1_{a+2} - r0_{a+2} r1_{a+1}, then s * conj(.)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int b = (a + 1) % 3, c = (a + 2) % 3;
+        T re = (u.r[0][b] * u.r[1][c] - u.i[0][b] * u.i[1][c])
+             - (u.r[0][c] * u.r[1][b] - u.i[0][c] * u.i[1][b]);
+        T im = (u.r[0][b] * u.i[1][c] + u.i[0][b] * u.r[1][c])
+             - (u.r[0][c] * u.i[1][b] + u.i[0][c] * u.r[1][b]);
+        u.r[2][a] = s * re;
+        u.i[2][a] = -s * im;
+    }
+}
+
+template <int P, int R> struct LinkIO;
+
+template <int R> struct LinkIO<P64, R> {
+    __device__ __forceinline__ static Mat3<double> load(const char *blk, int vh, int s, double sign)
+    {
+        const double2 *p = reinterpret_cast<const double2 *>(blk);
+        Mat3<double> u;
+        constexpr int n = R == 18 ? 9 : 6;
+#pragma unroll
+        for (int k = 0; k < n; ++k) {
+            double2 a = __ldg(p + (size_t)k * vh + s);
+            set_entry(u, k, a.x, a.y);
+        }
+        if (R == 12) reconstruct_row2(u, sign);
+        return u;
+    }
+};
+
+template <int R> struct LinkIO<P32, R> {
+    __device__ __forceinline__ static Mat3<float> load(const char *blk, int vh, int s, float sign)
+    {
+        const float4 *p = reinterpret_cast<const float4 *>(blk);
+        Mat3<float> u;
+        constexpr int n4 = R == 18 ? 4 : 3;
+#pragma unroll
+        for (int k = 0; k < n4; ++k) {
+            float4 a = __ldg(p + (size_t)k * vh + s);
+            set_entry(u, 2 * k, a.x, a.y);
+            set_entry(u, 2 * k + 1, a.z, a.w);
+        }
+        if (R == 18) {
+            float2 b = __ldg(reinterpret_cast<const float2 *>(p + (size_t)4 * vh) + s);
+            set_entry(u, 8, b.x, b.y);
+        } else {
+            reconstruct_row2(u, sign);
+        }
+        return u;
+    }
+};
+
+template <int R> struct LinkIO<P16, R> {
+    __device__ __forceinline__ static Mat3<float> load(const char *blk, int vh, int s, float sign)
+    {
+        const uint4 *p = reinterpret_cast<const uint4 *>(blk);
+        Mat3<float> u;
+        uint4 a = __ldg(p + s);
+        float2 e0 = h2_to_f2(a.x), e1 = h2_to_f2(a.y), e2 = h2_to_f2(a.z), e3 = h2_to_f2(a.w);
+        set_entry(u, 0, e0.x, e0.y);
+        set_entry(u, 1, e1.x, e1.y);
+        set_entry(u, 2, e2.x, e2.y);
+        set_entry(u, 3, e3.x, e3.y);
+        if (R == 18) {
+            uint4 b = __ldg(p + (size_t)vh + s);
+            float2 f0 = h2_to_f2(b.x), f1 = h2_to_f2(b.y), f2 = h2_to_f2(b.z), f3 = h2_to_f2(b.w);
+            set_entry(u, 4, f0.x, f0.y);
+            set_entry(u, 5, f1.x, f1.y);
+            set_entry(u, 6, f2.x, f2.y);
+            set_entry(u, 7, f3.x, f3.y);
+            unsigned c = __ldg(reinterpret_cast<const unsigned *>(p + (size_t)2 * vh) + s);
+            float2 g = h2_to_f2(c);
+            set_entry(u, 8, g.x, g.y);
+        } else {
+            uint2 b = __ldg(reinterpret_cast<const uint2 *>(p + (size_t)vh) + s);
+            float2 f0 = h2_to_f2(b.x), f1 = h2_to_f2(b.y);
+            set_entry(u, 4, f0.x, f0.y);
+            set_entry(u, 5, f1.x, f1.y);
+            reconstruct_row2(u, sign);
+        }
+        return u;
+    }
+};
+
+// acc += U v
+template <typename T>
+__device__ __forceinline__ void mul_add(const Mat3<T> &u, const Vec3<T> &v, Vec3<T> &acc)
+{
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            acc.r[a] += u.r[a][b] * v.r[b] - u.i[a][b] * v.i[b];
+            acc.i[a] += u.r[a][b] * v.i[b] + u.i[a][b] * v.r[b];
+        }
+}
+
+// acc -= U^dag v, (U^dag)_{ab} = conj(U_{ba})
+template <typename T>
+__device__ __forceinline__ void adj_mul_sub(const Mat3<T> &u, const Vec3<T> &v, Vec3<T> &acc)
+{
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            acc.r[a] -= u.r[b][a] * v.r[b] + u.i[b][a] * v.i[b];
+            acc.i[a] -= u.r[b][a] * v.i[b] - u.i[b][a] * v.r[b];
+        }
+}
+
+// ---------------------------------------------------------------------------
+// Solver state in device memory.  Kernels of one CG iteration read the
+// scalars they need from here, so an iteration is a fixed launch sequence
+// that can be captured once in a CUDA graph.
+// ---------------------------------------------------------------------------
+enum CGFlag { FLAG_RUN = 0, FLAG_CONVERGED = 1, FLAG_UPDATE = 2, FLAG_BREAKDOWN = 3,
+              FLAG_MAXITER = 4 };
+
+struct CGState {
+    double delta_new;  // r^dag r (iterated residual of the current precision)
+    double delta_old;
+    double pAp;        // d^dag A d
+    double alpha, beta;
+    double rmax2;      // largest |r|^2 since the last update (or at reset)
+    double stop_r2;    // tol^2 |b|^2: iterated-residual stopping point
+    double trig2;      // delta^2: reliable-update trigger (0 = never)
+    double m2;         // mass^2
+    double result;     // slot for stand-alone reductions
+    long long iter;        // iterations done (all precisions)
+    long long iter_limit;  // stop when iter reaches this
+    int flag;
+    int track_max;     // 1: rmax2 follows the running maximum (Sec. 3.2)
+    unsigned counter;  // arrival counter of the last-block reduction
+    unsigned pad;
+};
+
+// ---------------------------------------------------------------------------
+// Deterministic grid-wide FP64 sum: block partials, then the last block to
+// arrive sums them in a fixed order.  No floating-point atomics, no waiting:
+// the arrival counter only elects the block that finishes the sum.
+// ---------------------------------------------------------------------------
+template <int BS>
+__device__ __forceinline__ double block_sum(double v, double *sm)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sm[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (w == 0) {
+        s = (lane < BS / 32) ? sm[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    }
+    return s;  // valid in thread 0
+}
+
+// Returns true in thread 0 of the last block, with the grid total in `total`.
+template <int BS>
+__device__ __forceinline__ bool grid_sum(double v, double *partials, unsigned *counter,
+                                         double &total)
+{
+    __shared__ double sm[32];
+    __shared__ int is_last;
+    double s = block_sum<BS>(v, sm);
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = s;
+        __threadfence();
+        unsigned ticket = atomicAdd(counter, 1u);
+        is_last = (ticket == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!is_last) return false;
+    __threadfence();
+    double acc = 0.0;
+    for (int k = threadIdx.x; k < (int)gridDim.x; k += BS) acc += __ldcg(partials + k);
+    total = block_sum<BS>(acc, sm);
+    if (threadIdx.x == 0) {
+        *counter = 0u;
+        return true;
+    }
+    return false;
+}
+
+}  // namespace stg

@@ -1,0 +1,100 @@
+// Host-side structures shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "stg.h"
+#include "stg_common.cuh"
+
+namespace stg {
+
+constexpr int kBlock = 256;  // threads per block of every site-parallel kernel
+
+// Device copy of the links in one precision / reconstruction.
+struct LinkField {
+    char *base = nullptr;   // 8 blocks: (parity, mu) -> base + (2 * 4 ... ) see blk()
+    int prec = -1;
+    int recon = 18;
+    size_t blk_bytes = 0;   // bytes of one (parity, mu) block, 256-aligned
+    const char *blk(int parity, int mu) const { return base + (size_t)(parity * 4 + mu) * blk_bytes; }
+};
+
+struct Workspace;
+
+}  // namespace stg
+
+struct stg_gauge {
+    int dims[4];
+    stg::Geom geom;
+    int device;
+    int sloppy;             // stg_prec of the low-precision copy (P64 = none)
+    stg::LinkField hi;      // FP64 links
+    stg::LinkField lo;      // sloppy links (base == nullptr when sloppy == FP64)
+    stg::Workspace *ws;     // lazily created
+};
+
+namespace stg {
+
+// per-thread error text
+void set_error(const std::string &msg);
+stg_status cuda_fail(cudaError_t e, const char *what);
+
+#define STG_CUDA(call)                                                   \
+    do {                                                                 \
+        cudaError_t e_ = (call);                                         \
+        if (e_ != cudaSuccess) return ::stg::cuda_fail(e_, #call);       \
+    } while (0)
+
+#define STG_TRY(call)                                                    \
+    do {                                                                 \
+        stg_status s_ = (call);                                          \
+        if (s_ != STG_OK) return s_;                                     \
+    } while (0)
+
+Geom make_geom(const int dims[4]);
+
+const LinkField *links_for(const stg_gauge *g, int prec);
+
+// Reduction scratch: partial sums (one double per block) and the state.
+struct Workspace {
+    double *partials = nullptr;
+    size_t n_partials = 0;
+    CGState *state = nullptr;      // device
+    CGState *state_host = nullptr; // pinned mirror for read-back
+    void *tmp[3] = {nullptr, nullptr, nullptr};  // odd intermediate per precision
+    // CG vectors (allocated by the solver)
+    void *x64 = nullptr, *b64 = nullptr, *r64 = nullptr, *t64 = nullptr;
+    void *y = nullptr, *r = nullptr, *d = nullptr, *q = nullptr;
+    int cg_sloppy = -1;
+    cudaGraphExec_t graph = nullptr;
+    int graph_sloppy = -1, graph_iters = 0;
+};
+
+stg_status workspace_get(stg_gauge *g, Workspace **out);
+stg_status workspace_tmp(stg_gauge *g, int prec, void **out);
+void workspace_free(Workspace *ws);
+
+// kernels (launch only; all on `s`)
+enum Epi { EPI_NONE = 0, EPI_A = 1, EPI_A_DOT = 2, EPI_A_CG = 3, EPI_RES = 4, EPI_GATE = 5 };
+
+struct DslashLaunch {
+    const LinkField *links;
+    int out_parity;
+    const void *in;
+    void *out;
+    const void *w;   // EPI_A*: the even input d (m^2 d term, d^dag q); EPI_RES: b
+    const void *v;   // EPI_RES: x
+    double m2;
+    double *dot;     // EPI_A_DOT: result
+    CGState *state;  // EPI_A_CG, EPI_GATE
+    double *partials;
+    unsigned *counter;
+};
+
+stg_status launch_dslash(const Geom &g, int prec, int epi, const DslashLaunch &a, cudaStream_t s);
+
+int grid_for(long n);
+
+}  // namespace stg

@@ -1,0 +1,91 @@
+"""The C ABI library loads and exports every entry point declared in
+include/*.h; host-side argument checks that need no GPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for f in os.listdir(inc):
+        if f.endswith(".h"):
+            text = open(os.path.join(inc, f)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(stg_\w+)\s*\(", text))
+    return names
+
+
+@pytest.fixture(scope="module")
+def stg():
+    from paper_1111_0125_gb300 import build
+    build.build()
+    import paper_1111_0125_gb300 as m
+    return m
+
+
+def test_header_declares_the_entry_points():
+    names = _declared()
+    for want in ("stg_dslash", "stg_apply_A", "stg_cg_solve", "stg_gauge_create",
+                 "stg_gauge_destroy", "stg_pack_field", "stg_unpack_field"):
+        assert want in names
+
+
+def test_every_declared_symbol_is_exported(stg):
+    lib = ctypes.CDLL(stg.LIB_PATH)
+    for name in sorted(_declared()):
+        assert hasattr(lib, name), f"{name} declared in include/ but not exported"
+        assert hasattr(stg, name), f"{name} has no same-named Python binding"
+
+
+def test_library_is_built_for_sm_103a(stg):
+    from paper_1111_0125_gb300 import build
+    assert "arch=compute_103a,code=sm_103a" in build.ARCH
+
+
+def test_status_strings_and_version(stg):
+    assert stg.stg_version() >= 1
+    assert stg.stg_status_string(stg.STG_OK) == "ok"
+    assert "converged" in stg.stg_status_string(stg.STG_ERR_NOT_CONVERGED)
+    assert stg.stg_status_string(999) == "unknown status"
+
+
+def test_host_side_argument_checks(stg):
+    # rejected before any CUDA call
+    for dims in [(4, 4, 3, 4), (0, 4, 4, 4), (4, -2, 4, 4)]:
+        lx, ly, lz, lt = (abs(d) for d in dims)
+        links = np.zeros((max(lt, 1), max(lz, 1), max(ly, 1), max(lx, 1), 4, 3, 3), complex)
+        h = ctypes.c_void_p()
+        d = np.asarray(dims, np.int32)
+        st = stg.lib.stg_gauge_create(d.ctypes.data, links.ctypes.data, 1, 18, 0, ctypes.byref(h))
+        assert st == stg.STG_ERR_DIMS
+        assert "even" in stg.stg_last_error()
+    d = np.asarray((4, 4, 4, 4), np.int32)
+    h = ctypes.c_void_p()
+    assert stg.lib.stg_gauge_create(d.ctypes.data, None, 1, 18, 0, ctypes.byref(h)) == \
+        stg.STG_ERR_INVALID_ARG
+    links = np.zeros((4, 4, 4, 4, 4, 3, 3), complex)
+    assert stg.lib.stg_gauge_create(d.ctypes.data, links.ctypes.data, 1, 16, 0,
+                                    ctypes.byref(h)) == stg.STG_ERR_INVALID_ARG
+    assert stg.lib.stg_dslash(None, 0, 1, 2, 1, 0) == stg.STG_ERR_INVALID_ARG
+    assert stg.lib.stg_cg_solve(None, 1, 2, 0.1, 1e-10, None, None, 0) == \
+        stg.STG_ERR_INVALID_ARG
+    p = stg.stg_cg_params()
+    assert stg.lib.stg_cg_params_default(None, ctypes.byref(p)) == stg.STG_OK
+    assert p.policy == stg.STG_CG_RELIABLE and p.delta == 0.1
+    assert stg.lib.stg_gauge_destroy(None) == stg.STG_OK
+
+
+def test_product_path_never_imports_the_oracle():
+    pkg = os.path.join(ROOT, "paper_1111_0125_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in text and "from oracle" not in text, f
+                assert "stg_oracle" not in text and "liboracle" not in text, f

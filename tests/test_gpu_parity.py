@@ -1,0 +1,191 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (norm-wise relative error of the whole output field):
+  FP64 Dslash / A : 1e-12  (the kernel and the oracle differ only in the
+                            order of the 8 x 9 complex multiply-adds)
+  FP32            : 1e-6   (24-bit significand, ~10^2 rounding steps)
+  FP16 storage    : 2e-3   (11-bit significand on links and fields)
+CG: the true residual |b - A x| / |b| computed with the *oracle's* A is <= tol,
+and |x - x_oracle| / |x_oracle| <= kappa_hat * tol, kappa_hat = (m^2+64)/m^2.
+"""
+import numpy as np
+import pytest
+import torch
+
+import gen
+import oracle
+import paper_1111_0125_gb300 as stg
+from paper_1111_0125_gb300 import Gauge
+
+pytestmark = pytest.mark.gpu
+
+TOL = {stg.STG_FP64: 1e-12, stg.STG_FP32: 1e-6, stg.STG_FP16: 2e-3}
+
+# several tiles and ragged tails: Vh = 128, 8, 192, 1440, 2520, 20736
+DIMS = [(4, 4, 4, 4), (2, 2, 2, 2), (4, 6, 2, 8), (6, 4, 10, 12), (10, 6, 6, 14),
+        (12, 12, 12, 24)]
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _links(dims, kind="haar", seed=0, eps=0.5):
+    return gen.gauge_field(dims, kind, seed=seed, eps=eps)
+
+
+def _to_dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    oracle.build()
+    yield
+    torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("prec", [stg.STG_FP64, stg.STG_FP32, stg.STG_FP16])
+def test_pack_unpack_roundtrip(prec):
+    dims = (6, 4, 10, 12)
+    U = _links(dims)
+    chi = gen.source(dims, seed=4)
+    with Gauge(dims, U, sloppy=prec if prec != stg.STG_FP64 else stg.STG_FP64) as g:
+        back = g.unpack(g.pack(_to_dev(chi), prec), prec).cpu().numpy()
+    if prec == stg.STG_FP64:
+        assert np.array_equal(back, chi)
+    else:
+        assert rel(back, chi) < {stg.STG_FP32: 1e-7, stg.STG_FP16: 1e-3}[prec]
+
+
+@pytest.mark.parametrize("dims", DIMS)
+@pytest.mark.parametrize("prec,recon", [(stg.STG_FP64, 18), (stg.STG_FP64, 12),
+                                        (stg.STG_FP32, 18), (stg.STG_FP32, 12),
+                                        (stg.STG_FP16, 18), (stg.STG_FP16, 12)])
+def test_dslash_matches_oracle(dims, prec, recon):
+    U = _links(dims, "haar", seed=sum(dims))
+    with Gauge(dims, U, sloppy=prec, recon=recon) as g:
+        for parity in (0, 1):
+            chi = gen.source(dims, seed=parity + 7)
+            out = g.unpack(g.dslash(g.pack(_to_dev(chi), prec), parity, prec), prec)
+            want = oracle.dslash(dims, U, chi, out_parity=parity)
+            assert rel(out.cpu().numpy(), want) < TOL[prec], (dims, prec, recon, parity)
+
+
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (6, 4, 10, 12), (12, 12, 12, 24)])
+@pytest.mark.parametrize("prec,recon", [(stg.STG_FP64, 18), (stg.STG_FP32, 18),
+                                        (stg.STG_FP32, 12), (stg.STG_FP16, 12)])
+def test_apply_A_and_dot_match_oracle(dims, prec, recon):
+    U = _links(dims, "exp", seed=3, eps=0.4)
+    mass = 0.05
+    chi = gen.source(dims, seed=5)
+    want = oracle.apply_A(dims, U, mass, chi)
+    with Gauge(dims, U, sloppy=prec, recon=recon) as g:
+        f = g.pack(_to_dev(chi), prec)
+        out = g.unpack(g.apply_A(f, mass, prec), prec).cpu().numpy()
+        assert rel(out, want) < TOL[prec]
+        out2, dot = g.apply_A_dot(f, mass, prec)
+        out2 = g.unpack(out2, prec).cpu().numpy()
+        assert np.array_equal(out, out2)
+        chi_r = g.unpack(f, prec).cpu().numpy()  # the rounded input the kernel saw
+        want_dot = np.vdot(chi_r, out2).real
+        assert abs(dot.item() - want_dot) <= TOL[prec] * abs(want_dot) * 10
+        # fixed summation order: bitwise reproducible
+        _, dot_b = g.apply_A_dot(f, mass, prec)
+        assert dot_b.item() == dot.item()
+
+
+def test_free_field_closed_form_on_gpu():
+    """U = 1: A phi = (m^2 + 4 sum sin^2 p) phi on a plane wave (no oracle)."""
+    import lattice_util as lu
+    dims = (8, 4, 6, 8)
+    mass = 0.3
+    p = lu.momentum(dims, (1, 1, 2, 0))
+    phi = lu.plane_wave(dims, p, [1.0, 0.5j, -0.25])
+    with Gauge(dims, gen.unit_gauge(dims), sloppy=stg.STG_FP64) as g:
+        out = g.unpack(g.apply_A(g.pack(_to_dev(phi), stg.STG_FP64), mass, stg.STG_FP64),
+                       stg.STG_FP64).cpu().numpy()
+    assert rel(out, lu.free_eigenvalue(p, mass) * phi) < 1e-13
+
+
+def _check_solution(dims, U, mass, b, x, tol, x_ref=None):
+    r = b - oracle.apply_A(dims, U, mass, x)
+    tr = np.linalg.norm(r) / np.linalg.norm(b)
+    assert tr <= tol, tr
+    if x_ref is not None:
+        kappa = (mass ** 2 + 64) / mass ** 2
+        assert rel(x, x_ref) <= kappa * tol
+    return tr
+
+
+def test_cg_fp64_c1():
+    """4^4, Haar links seed 0, source seed 1, m = 0.1, tol 1e-10, plain FP64 CG."""
+    dims, mass, tol = (4, 4, 4, 4), 0.1, 1e-10
+    U = gen.gauge_field(dims, "haar", seed=0)
+    b = gen.source(dims, seed=1)
+    x_ref, info = oracle.cg(dims, U, mass, b, tol=tol)
+    with Gauge(dims, U, sloppy=stg.STG_FP64) as g:
+        x, st = g.cg_solve(_to_dev(b), mass, tol, g.params(policy=stg.STG_CG_PLAIN))
+    _check_solution(dims, U, mass, b, x.cpu().numpy(), tol, x_ref)
+    assert st["true_res"] <= tol and st["sloppy_iters"] == 0
+    # the same iteration as the oracle's Fig. 1 loop, up to rounding order
+    assert abs(st["iters"] - info["iters"]) <= max(3, info["iters"] // 20)
+
+
+@pytest.mark.parametrize("sloppy,recon", [(stg.STG_FP32, 18), (stg.STG_FP32, 12),
+                                          (stg.STG_FP16, 12), (stg.STG_FP16, 18)])
+@pytest.mark.parametrize("policy", [stg.STG_CG_RELIABLE, stg.STG_CG_REFINE])
+def test_cg_mixed_matches_oracle(sloppy, recon, policy):
+    dims, mass, tol = (8, 8, 8, 8), 0.05, 1e-10
+    U = gen.gauge_field(dims, "exp", seed=11, eps=0.4)
+    b = gen.source(dims, seed=12)
+    x_ref, _ = oracle.cg(dims, U, mass, b, tol=1e-12)
+    with Gauge(dims, U, sloppy=sloppy, recon=recon) as g:
+        x, st = g.cg_solve(_to_dev(b), mass, tol, g.params(policy=policy))
+    _check_solution(dims, U, mass, b, x.cpu().numpy(), tol, x_ref)
+    assert st["sloppy_iters"] == st["iters"] > 0 and st["updates"] >= 1
+
+
+def test_cg_initial_guess_and_zero_source():
+    dims, mass = (4, 4, 4, 8), 0.2
+    U = gen.gauge_field(dims, "haar", seed=2)
+    b = gen.source(dims, seed=3)
+    with Gauge(dims, U, sloppy=stg.STG_FP32) as g:
+        x, st = g.cg_solve(_to_dev(b), mass, 1e-10)
+        x2, st2 = g.cg_solve(_to_dev(b), mass, 1e-10, x0=x)
+        assert st2["iters"] == 0 and torch.equal(x, x2)
+        z, st3 = g.cg_solve(torch.zeros_like(x), mass, 1e-10, x0=x)
+        assert st3["iters"] == 0 and not z.any()
+
+
+def test_cg_errors():
+    dims = (4, 4, 4, 4)
+    U = gen.gauge_field(dims, "haar", seed=0)
+    b = gen.source(dims, seed=1)
+    with Gauge(dims, U, sloppy=stg.STG_FP32) as g:
+        with pytest.raises(stg.StgError) as e:
+            g.cg_solve(_to_dev(b), 0.01, 1e-10, g.params(maxiter=5))
+        assert e.value.status == stg.STG_ERR_NOT_CONVERGED
+        assert e.value.stats["iters"] >= 5 and e.value.stats["true_res"] > 1e-10
+        bad = b.copy()
+        bad[3, 1] = np.nan
+        with pytest.raises(stg.StgError) as e:
+            g.cg_solve(_to_dev(bad), 0.1, 1e-10)
+        assert e.value.status == stg.STG_ERR_INVALID_ARG
+        with pytest.raises(stg.StgError) as e:
+            g.cg_solve(_to_dev(b), 0.1, 0.0)
+        assert e.value.status == stg.STG_ERR_INVALID_ARG
+        f = g.pack(_to_dev(b), stg.STG_FP16)
+        with pytest.raises(stg.StgError) as e:   # handle holds FP64 + FP32 only
+            g.dslash(f, 1, stg.STG_FP16)
+        assert e.value.status == stg.STG_ERR_UNSUPPORTED
+        with pytest.raises(stg.StgError) as e:
+            stg.stg_dslash(g.handle, 2, f, f, stg.STG_FP32)
+        assert e.value.status == stg.STG_ERR_INVALID_ARG
+
+
+def test_gauge_create_rejects_bad_dims():
+    with pytest.raises(stg.StgError) as e:
+        stg.stg_gauge_create((4, 4, 3, 4), np.zeros((4, 3, 4, 4, 4, 3, 3), complex))
+    assert e.value.status == stg.STG_ERR_DIMS
