@@ -1,0 +1,398 @@
+#!/usr/bin/env python
+"""Benchmark of the staggered-fermion CG hot path on GB300.
+
+One step = one complete mixed-precision CG solve A x = b to a true residual
+|b - A x| <= 1e-10 |b| on a 32^3 x 64 lattice (m = 0.005, exp(i 0.6 H) SU(3)
+links, complex Gaussian source), i.e. every kernel of the path: Dslash
+half-passes, the fused A operator with d^dag A d, the CG vector updates and
+the FP64 reliable updates.  Inputs are resident in HBM when the timed region
+starts; the working set (links 403 MB at FP32 / 12-real) is larger than L2.
+
+Prints one JSON line (rank 0).  `value` = solves per second over all ranks
+(each rank solves its own system: replicas, weak scaling).  Also reports the
+time of the GPU's own plain FP64 CG on the same system, the roofline of the
+dominant kernel from CUDA events recorded inside the solver's graph, an
+end-to-end figure with host buffers, the clocks seen during the timed region
+and the FP64 CPU oracle timed on the host cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl stg|reference]
+  python bench.py --kernels-only --reps 3     # kernels alone (for ncu)
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+LINK_BYTES = {("f64", 18): 144, ("f64", 12): 96, ("f32", 18): 72, ("f32", 12): 48,
+              ("f16", 18): 36, ("f16", 12): 24}
+FIELD_BYTES = {"f64": 48, "f32": 24, "f16": 16}
+FALLBACK_HBM_GBS = 6800.0
+WORKLOAD = "32^3x64 staggered mixed-precision CG to 1e-10 true residual"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="stg", choices=["stg", "reference"])
+    ap.add_argument("--lattice", default="32,32,32,64")
+    ap.add_argument("--sloppy", default="f32", choices=["f32", "f16"])
+    ap.add_argument("--recon", type=int, default=12, choices=[12, 18])
+    ap.add_argument("--mass", type=float, default=0.005)
+    ap.add_argument("--tol", type=float, default=1e-10)
+    ap.add_argument("--eps", type=float, default=0.6)
+    ap.add_argument("--delta", type=float, default=0.1)
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 CG comparison")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--kernels-only", action="store_true")
+    ap.add_argument("--reps", type=int, default=3)
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_uuid: str):
+        self.uuid = gpu_uuid
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        mine = [r for r in rows if self.uuid and r[0] == self.uuid]
+        rows = mine if mine else rows
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# roofline bookkeeping
+# ---------------------------------------------------------------------------
+def measured_hbm():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("dslash.cu", "stg_common.cuh"):
+        with open(os.path.join(ROOT, "paper_1111_0125_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_key: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source (hash match); else None."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    try:
+        with open(p) as f:
+            lines = f.read().splitlines()
+    except OSError:
+        return None
+    src = [ln.split(":", 1)[1].strip() for ln in lines if ln.startswith("source_hash:")]
+    if not src or src[0] != kernel_source_hash():
+        return None
+    for ln in lines:
+        if ln.startswith(f"traffic {kernel_key}:"):
+            return float(ln.split(":", 1)[1].split()[0])
+    return None
+
+
+def dslash_bytes(vh, prec, recon, extra_fields):
+    """Compulsory bytes of one half-pass: 8 links + input + output (+ extra
+    streamed fields of the fused epilogue)."""
+    return vh * (8 * LINK_BYTES[(prec, recon)] + (2 + extra_fields) * FIELD_BYTES[prec])
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline and reference arm)
+# ---------------------------------------------------------------------------
+def oracle_sample(dims, U, mass, b, fp64_iters, budget_s):
+    """Time the FP64 oracle CG (as it stands) for a bounded number of
+    iterations on the full lattice and scale to a complete solve."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    oracle.cg(dims, U, mass, b, tol=0.0, maxiter=1, max_restarts=0)
+    t1 = time.perf_counter() - t0          # 1 iteration + 2 A for the residuals
+    n = max(2, min(200, int(budget_s / max(t1 / 3.0, 1e-6))))
+    t0 = time.perf_counter()
+    oracle.cg(dims, U, mass, b, tol=0.0, maxiter=n, max_restarts=0)
+    tn = time.perf_counter() - t0
+    per_iter = (tn - t1) / (n - 1)
+    solve_s = per_iter * fp64_iters + (t1 - per_iter)
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": 1.0 / solve_s, "unit": "solves/s", "cores": cores, "kind": "oracle",
+            "sample": f"{n} FP64 CG iterations of the oracle on the full {dims} lattice "
+                      f"({tn:.1f} s), scaled to {fp64_iters} iterations (the GPU FP64 CG count)",
+            "seconds_per_solve": solve_s}
+
+
+def gen_inputs(dims, eps, rank):
+    import gen
+    U = gen.gauge_field(dims, "exp", seed=0, eps=eps)
+    b = gen.source(dims, seed=1 + rank)
+    return U, b
+
+
+def run_reference(args, dims):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    U, b = gen_inputs(dims, args.eps, 0)
+    fp64_iters = 2552 if dims == (32, 32, 32, 64) else 3 * (dims[0] * dims[1] * dims[2] * dims[3] // 2)
+    per_step = max(5.0, 60.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        oracle_sample(dims, U, args.mass, b, fp64_iters, min(per_step, 5.0))
+    vals = []
+    for _ in range(args.steps):
+        vals.append(oracle_sample(dims, U, args.mass, b, fp64_iters, per_step))
+    v = statistics.median(x["value"] for x in vals)
+    cb = dict(vals[-1])
+    cb["value"] = v
+    ms = 1000.0 / v
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config_dict(args, dims),
+        "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
+        "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+METRIC = "Dslash GB/s vs HBM peak; CG time to 1e-10 residual mixed vs FP64; p99 latency"
+
+
+def config_dict(args, dims):
+    return {"workload": WORKLOAD, "lattice": "x".join(str(d) for d in dims),
+            "mass": args.mass, "tol": args.tol, "links": f"exp(i*{args.eps}*H) SU(3), seed 0",
+            "source": "complex Gaussian, seed 1+rank", "sloppy": args.sloppy,
+            "recon": args.recon, "reliable_delta": args.delta, "policy": "reliable",
+            "l2": "inputs larger than L2 (links alone exceed 129 MB); no flush",
+            "parallelism": f"replicas{args.gpus}"}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def main():
+    args = parse()
+    dims = tuple(int(v) for v in args.lattice.split(","))
+    if args.impl == "reference":
+        run_reference(args, dims)
+        return
+    import numpy as np
+    import torch
+    import paper_1111_0125_gb300 as stg
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    sloppy = {"f32": stg.STG_FP32, "f16": stg.STG_FP16}[args.sloppy]
+    U, b_np = gen_inputs(dims, args.eps, rank)
+    vh = b_np.shape[0]
+    g = stg.Gauge(dims, U, sloppy=sloppy, recon=args.recon)
+    stream = torch.cuda.current_stream()
+    b = torch.from_numpy(b_np).to(dev)
+
+    if args.kernels_only:
+        f = g.pack(b, sloppy)
+        out = g.new_field(sloppy)
+        f64 = g.pack(b, stg.STG_FP64)
+        o64 = g.new_field(stg.STG_FP64)
+        for _ in range(args.reps):
+            g.dslash(f, 1, sloppy, out=out)
+            g.apply_A(f, args.mass, sloppy, out=out)
+        for _ in range(args.reps):
+            g.dslash(f64, 1, stg.STG_FP64, out=o64)
+        torch.cuda.synchronize()
+        if rank == 0:
+            print(json.dumps({"kernels_only": True, "lattice": dims, "reps": args.reps}))
+        return
+
+    params = g.params(policy=stg.STG_CG_RELIABLE, sloppy=sloppy, delta=args.delta, timing=1)
+
+    def solve():
+        x = torch.zeros_like(b)
+        return x, stg.stg_cg_solve(g.handle, b, x, args.mass, args.tol, params, stream)
+
+    for _ in range(args.warmup):
+        solve()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    gpu_id = ""
+    try:
+        gpu_id = str(torch.cuda.get_device_properties(dev).uuid)
+        if not gpu_id.startswith("GPU-"):
+            gpu_id = "GPU-" + gpu_id
+    except Exception:
+        pass
+    barrier()
+    clocks = ClockSampler(gpu_id)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stats = []
+    ev0.record(stream)
+    for _ in range(args.steps):
+        x, st = solve()
+        stats.append(st)
+    ev1.record(stream)
+    barrier()
+    ck = clocks.stop()
+    elapsed = ev0.elapsed_time(ev1) / 1000.0
+    if dist is not None:
+        t = torch.tensor([elapsed], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    value = world * args.steps / elapsed
+    ms_step = 1000.0 * elapsed / args.steps
+
+    # true residual of the last solution with the FP64 operator on the GPU
+    st_last = stats[-1]
+
+    # end to end: host buffers, H2D of b and D2H of x inside the timed region
+    b_host = torch.from_numpy(b_np).pin_memory()
+    x_host = torch.empty_like(b_host).pin_memory()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        bd = b_host.to(dev, non_blocking=True)
+        xd = torch.zeros_like(bd)
+        stg.stg_cg_solve(g.handle, bd, xd, args.mass, args.tol, params, stream)
+        x_host.copy_(xd, non_blocking=True)
+        stream.synchronize()
+    e1.record(stream)
+    barrier()
+    e2e_s = e0.elapsed_time(e1) / 1000.0
+    if dist is not None:
+        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    # the GPU's own plain FP64 CG on the same system
+    fp64 = None
+    if not args.no_fp64:
+        p64 = g.params(policy=stg.STG_CG_PLAIN, sloppy=stg.STG_FP64, timing=1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        x64 = torch.zeros_like(b)
+        s64 = stg.stg_cg_solve(g.handle, b, x64, args.mass, args.tol, p64, stream)
+        fp64 = {"seconds": time.perf_counter() - t0, "iters": s64["iters"],
+                "true_res": s64["true_res"], "t_dslash_ms": s64["t_dslash_ms"]}
+
+    if rank != 0:
+        return
+    # roofline of the dominant kernel (live, from events inside the graph)
+    t_gate = statistics.mean(s["t_dslash_ms"] for s in stats)
+    t_a = statistics.mean(s["t_dslash_a_ms"] for s in stats)
+    if t_a >= t_gate:
+        kname, kkey, tk, nbytes = ("k_dslash (q = m^2 d - D_eo t, fused d^dag q)", "dslash_a",
+                                   t_a, dslash_bytes(vh, args.sloppy, args.recon, 1))
+    else:
+        kname, kkey, tk, nbytes = ("k_dslash (t = D_oe d)", "dslash",
+                                   t_gate, dslash_bytes(vh, args.sloppy, args.recon, 0))
+    peak, peak_src = measured_hbm()
+    achieved = nbytes / (tk / 1000.0) / 1e9
+    iters = statistics.mean(s["iters"] for s in stats)
+    updates = statistics.mean(s["updates"] for s in stats)
+    cpu = None
+    if not args.no_cpu and world == 1:
+        cpu = oracle_sample(dims, U, args.mass, b_np, fp64["iters"] if fp64 else 2552,
+                            args.cpu_seconds)
+        cpu.pop("seconds_per_solve")
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": args.sloppy, "data": "synthetic",
+        "config": config_dict(args, dims),
+        "cg": {"mixed_seconds": ms_step / 1000.0, "iters": iters, "updates": updates,
+               "low_precision_fraction": iters / (iters + updates),
+               "true_res": st_last["true_res"],
+               "fp64_seconds": fp64["seconds"] if fp64 else None,
+               "fp64_iters": fp64["iters"] if fp64 else None,
+               "speedup_vs_fp64": (fp64["seconds"] / (ms_step / 1000.0)) if fp64 else None,
+               "fp64_dslash_ms": fp64["t_dslash_ms"] if fp64 else None,
+               "kernel_ms": {"dslash": t_gate, "dslash_a": t_a,
+                             "update": statistics.mean(s["t_update_ms"] for s in stats),
+                             "xpay": statistics.mean(s["t_xpay_ms"] for s in stats)}},
+        "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
+                     "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": ncu_traffic(f"{kkey}_{args.sloppy}_{args.recon}"),
+                     "algorithmic_bytes_per_launch": nbytes, "launch_ms": tk,
+                     "gflops_576": vh * 576 / (tk / 1000.0) / 1e9},
+        "cpu_baseline": cpu,
+        "e2e": {"value": world * args.steps / e2e_s, "unit": "solves/s",
+                "h2d_bytes_per_step": int(b_host.numel() * 16),
+                "d2h_bytes_per_step": int(x_host.numel() * 16)},
+        "gpu_launches": int(sum(s["launches"] for s in stats)),
+        "clocks": ck,
+    }
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -91,6 +91,9 @@ typedef struct stg_cg_params {
     long maxiter;      /* bound on the total iteration count (0 = 10 N_dim,
                           N_dim = 3 Vh as in Fig. 1)                           */
     int check_every;   /* inner iterations between host checks (0 = auto)     */
+    int timing;        /* 1: time the four kernels of one inner iteration per
+                          check with CUDA events recorded inside the solver's
+                          graph (stats.t_*); 0: no events                     */
 } stg_cg_params;
 
 typedef struct stg_cg_stats {
@@ -100,6 +103,12 @@ typedef struct stg_cg_stats {
     double true_res;       /* |b - A x| / |b| with the FP64 operator at exit   */
     double iter_res;       /* iterated residual / |b| at exit                  */
     double seconds;        /* wall time of the solve (host clock)              */
+    long launches;         /* kernels enqueued by the solve (graph nodes count) */
+    long timed_iters;      /* inner iterations that carried timing events       */
+    double t_dslash_ms;    /* mean duration: first half-pass t = D_oe d          */
+    double t_dslash_a_ms;  /* mean duration: q = m^2 d - D_eo t with d^dag q     */
+    double t_update_ms;    /* mean duration: y += alpha d, r -= alpha q, |r|^2   */
+    double t_xpay_ms;      /* mean duration: d = r + beta d                      */
 } stg_cg_stats;
 
 typedef struct stg_gauge stg_gauge; /* opaque */
@@ -189,7 +198,8 @@ stg_status stg_apply_A_dot(const stg_gauge *g, double mass, const void *in_dev,
                            stg_stream_t stream);
 
 /* Fill params with the defaults: RELIABLE, sloppy = handle's sloppy
- * precision, delta = 0.1, maxiter = 0 (10 N_dim), check_every = 0 (auto). */
+ * precision, delta = 0.1, maxiter = 0 (10 N_dim), check_every = 0 (auto),
+ * timing = 0. */
 stg_status stg_cg_params_default(const stg_gauge *g, stg_cg_params *params);
 
 /*

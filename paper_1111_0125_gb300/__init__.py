@@ -47,13 +47,16 @@ _STATUS = {STG_OK: "ok", STG_ERR_INVALID_ARG: "invalid argument",
 class stg_cg_params(ctypes.Structure):
     _fields_ = [("policy", ctypes.c_int), ("sloppy", ctypes.c_int),
                 ("delta", ctypes.c_double), ("maxiter", ctypes.c_long),
-                ("check_every", ctypes.c_int)]
+                ("check_every", ctypes.c_int), ("timing", ctypes.c_int)]
 
 
 class stg_cg_stats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_long), ("sloppy_iters", ctypes.c_long),
                 ("updates", ctypes.c_long), ("true_res", ctypes.c_double),
-                ("iter_res", ctypes.c_double), ("seconds", ctypes.c_double)]
+                ("iter_res", ctypes.c_double), ("seconds", ctypes.c_double),
+                ("launches", ctypes.c_long), ("timed_iters", ctypes.c_long),
+                ("t_dslash_ms", ctypes.c_double), ("t_dslash_a_ms", ctypes.c_double),
+                ("t_update_ms", ctypes.c_double), ("t_xpay_ms", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

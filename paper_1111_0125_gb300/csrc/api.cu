@@ -248,6 +248,7 @@ stg_status stg_cg_params_default(const stg_gauge *g, stg_cg_params *p)
     p->delta = 0.1;
     p->maxiter = 0;
     p->check_every = 0;
+    p->timing = 0;
     return STG_OK;
 }
 

@@ -200,8 +200,9 @@ static stg_status norm2(const Geom &g, int prec, const void *v, Workspace *ws, c
     return STG_OK;
 }
 
-// one CG iteration on the sloppy vectors (4 launches)
-static stg_status iteration(stg_gauge *gg, Workspace *ws, int pd, cudaStream_t s)
+// one CG iteration on the sloppy vectors (4 launches); with `ev`, CUDA
+// events are recorded before and after each kernel (5 events)
+static stg_status iteration(stg_gauge *gg, Workspace *ws, int pd, cudaStream_t s, cudaEvent_t *ev)
 {
     const Geom &g = gg->geom;
     const LinkField *lf = links_for(gg, pd);
@@ -211,19 +212,24 @@ static stg_status iteration(stg_gauge *gg, Workspace *ws, int pd, cudaStream_t s
     L.state = ws->state;
     L.partials = ws->partials;
     L.counter = &ws->state->counter;
+    if (ev) STG_CUDA(cudaEventRecord(ev[0], s));
     // the state flag gates every kernel, including the first half-pass
     L.out_parity = 1;
     L.in = ws->d;
     L.out = t;
     STG_TRY(launch_dslash(g, pd, EPI_GATE, L, s));
+    if (ev) STG_CUDA(cudaEventRecord(ev[1], s));
     L.out_parity = 0;
     L.in = t;
     L.out = ws->q;
     L.w = ws->d;
     STG_TRY(launch_dslash(g, pd, EPI_A_CG, L, s));
+    if (ev) STG_CUDA(cudaEventRecord(ev[2], s));
     const int grid = grid_for(g.Vh);
     STG_DISPATCH_PD(pd, k_cg_update, g.Vh, ws->y, ws->r, ws->d, ws->q, ws->state, ws->partials);
+    if (ev) STG_CUDA(cudaEventRecord(ev[3], s));
     STG_DISPATCH_PD(pd, k_xpay, g.Vh, ws->r, ws->d, ws->state);
+    if (ev) STG_CUDA(cudaEventRecord(ev[4], s));
     STG_CUDA(cudaGetLastError());
     return STG_OK;
 }
@@ -275,9 +281,11 @@ static stg_status prepare(stg_gauge *g, Workspace *ws, int pd)
 
 // Capture `n` iterations as a graph on a private stream (capture is not
 // allowed on the legacy default stream), replayed on the caller's stream.
-static stg_status get_graph(stg_gauge *g, Workspace *ws, int pd, int n, cudaGraphExec_t *out)
+// With timing, the first iteration of the chunk records the 5 events.
+static stg_status get_graph(stg_gauge *g, Workspace *ws, int pd, int n, int timing,
+                            cudaGraphExec_t *out)
 {
-    if (ws->graph && ws->graph_sloppy == pd && ws->graph_iters == n) {
+    if (ws->graph && ws->graph_sloppy == pd && ws->graph_iters == n && ws->graph_timing == timing) {
         *out = ws->graph;
         return STG_OK;
     }
@@ -285,13 +293,16 @@ static stg_status get_graph(stg_gauge *g, Workspace *ws, int pd, int n, cudaGrap
         cudaGraphExecDestroy(ws->graph);
         ws->graph = nullptr;
     }
+    if (timing && !ws->ev[0])
+        for (int k = 0; k < 5; ++k) STG_CUDA(cudaEventCreate(&ws->ev[k]));
     cudaStream_t cs;
     STG_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     stg_status st = STG_OK;
     if (e == cudaSuccess) {
-        for (int k = 0; k < n && st == STG_OK; ++k) st = iteration(g, ws, pd, cs);
+        for (int k = 0; k < n && st == STG_OK; ++k)
+            st = iteration(g, ws, pd, cs, (timing && k == 0) ? ws->ev : nullptr);
         cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
         if (st == STG_OK && e2 != cudaSuccess) st = cuda_fail(e2, "cudaStreamEndCapture");
     } else {
@@ -309,6 +320,7 @@ static stg_status get_graph(stg_gauge *g, Workspace *ws, int pd, int n, cudaGrap
     if (st != STG_OK) return st;
     ws->graph_sloppy = pd;
     ws->graph_iters = n;
+    ws->graph_timing = timing;
     *out = ws->graph;
     return STG_OK;
 }
@@ -367,6 +379,8 @@ stg_status cg_solve(stg_gauge *g, const double *src, double *x, double mass, dou
     const long maxiter = p->maxiter > 0 ? p->maxiter : 10L * 3L * geo.Vh;
     int chunk = p->check_every > 0 ? p->check_every : (geo.Vh >= (1 << 19) ? 16 : 32);
     if (chunk > 256) chunk = 256;
+    long launches = 0;
+    double tsum[4] = {0.0, 0.0, 0.0, 0.0};
 
     // b, x0 into the FP64 device layout; |b|^2
     STG_TRY(pack_field(geo, P64, src, ws->b64, s));
@@ -419,7 +433,7 @@ stg_status cg_solve(stg_gauge *g, const double *src, double *x, double mass, dou
         h->counter = 0;
         if (status == STG_OK) status = write_state(ws, s);
         cudaGraphExec_t graph = nullptr;
-        if (status == STG_OK) status = get_graph(g, ws, pd, chunk, &graph);
+        if (status == STG_OK) status = get_graph(g, ws, pd, chunk, p->timing ? 1 : 0, &graph);
         int breakdowns = 0;
         while (status == STG_OK) {
             cudaError_t e = cudaGraphLaunch(graph, s);
@@ -429,6 +443,20 @@ stg_status cg_solve(stg_gauge *g, const double *src, double *x, double mass, dou
             }
             status = read_state(ws, s);
             if (status != STG_OK) break;
+            launches += 4L * chunk;
+            if (p->timing) {
+                // the chunk's first iteration always runs: a chunk starts with the flag down
+                float ms[4];
+                bool ok = true;
+                for (int k = 0; k < 4 && ok; ++k)
+                    ok = cudaEventElapsedTime(&ms[k], ws->ev[k], ws->ev[k + 1]) == cudaSuccess;
+                if (ok) {
+                    tsum[0] += ms[0]; tsum[1] += ms[1]; tsum[2] += ms[2]; tsum[3] += ms[3];
+                    st.timed_iters += 1;
+                } else {
+                    cudaGetLastError();
+                }
+            }
             const int flag = h->flag;
             if (flag == FLAG_RUN) continue;
             // Sec. 3.2 update: x_{k+1} = x_k + y_n (FP64), r_{k+1} = b - A x_{k+1}
@@ -483,6 +511,16 @@ stg_status cg_solve(stg_gauge *g, const double *src, double *x, double mass, dou
         if (u != STG_OK) status = u;
         else if (e != cudaSuccess) status = cuda_fail(e, "cudaStreamSynchronize");
     }
+    if (st.timed_iters > 0) {
+        st.t_dslash_ms = tsum[0] / st.timed_iters;
+        st.t_dslash_a_ms = tsum[1] / st.timed_iters;
+        st.t_update_ms = tsum[2] / st.timed_iters;
+        st.t_xpay_ms = tsum[3] / st.timed_iters;
+    }
+    // setup: 2 packs, norm, residual (2), reset; per update: accumulate,
+    // residual (2), reset; final unpack
+    launches += 6 + 4L * st.updates + 1;
+    st.launches = launches;
     st.iters = (long)h->iter;
     st.sloppy_iters = plain ? 0 : (long)h->iter;
     st.true_res = sqrt(rr / bb);

@@ -288,6 +288,8 @@ void workspace_free(Workspace *ws)
 {
     if (!ws) return;
     if (ws->graph) cudaGraphExecDestroy(ws->graph);
+    for (int k = 0; k < 5; ++k)
+        if (ws->ev[k]) cudaEventDestroy(ws->ev[k]);
     cudaFree(ws->partials);
     cudaFree(ws->state);
     if (ws->state_host) cudaFreeHost(ws->state_host);

@@ -69,7 +69,8 @@ struct Workspace {
     void *y = nullptr, *r = nullptr, *d = nullptr, *q = nullptr;
     int cg_sloppy = -1;
     cudaGraphExec_t graph = nullptr;
-    int graph_sloppy = -1, graph_iters = 0;
+    int graph_sloppy = -1, graph_iters = 0, graph_timing = 0;
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // timing events
 };
 
 stg_status workspace_get(stg_gauge *g, Workspace **out);
