@@ -354,6 +354,23 @@ def main():
     else:
         kname, kkey, tk, nbytes = ("k_dslash (t = D_oe d)", "dslash",
                                    t_gate, dslash_bytes(vh, args.sloppy, args.recon, 0))
+    tk_source = "events inside the solver graph, timed region"
+    if not tk > 0.0:
+        # fallback: the same kernel family launched stand-alone on this stream
+        f = g.pack(b, sloppy)
+        out = g.new_field(sloppy)
+        for _ in range(3):
+            g.dslash(f, 1, sloppy, out=out)
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        for _ in range(20):
+            g.dslash(f, 1, sloppy, out=out)
+        s1.record(stream)
+        s1.synchronize()
+        kname, kkey = "k_dslash (t = D_oe d)", "dslash"
+        tk = s0.elapsed_time(s1) / 20
+        nbytes = dslash_bytes(vh, args.sloppy, args.recon, 0)
+        tk_source = "stand-alone launches after the timed region"
     peak, peak_src = measured_hbm()
     achieved = nbytes / (tk / 1000.0) / 1e9
     iters = statistics.mean(s["iters"] for s in stats)
@@ -383,6 +400,7 @@ def main():
                      "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": ncu_traffic(f"{kkey}_{args.sloppy}_{args.recon}"),
                      "algorithmic_bytes_per_launch": nbytes, "launch_ms": tk,
+                     "launch_ms_source": tk_source,
                      "gflops_576": vh * 576 / (tk / 1000.0) / 1e9},
         "cpu_baseline": cpu,
         "e2e": {"value": world * args.steps / e2e_s, "unit": "solves/s",

@@ -201,7 +201,8 @@ static stg_status norm2(const Geom &g, int prec, const void *v, Workspace *ws, c
 }
 
 // one CG iteration on the sloppy vectors (4 launches); with `ev`, CUDA
-// events are recorded before and after each kernel (5 events)
+// events are recorded before and after each kernel (5 events; external
+// records, so that stream capture turns them into event-record nodes)
 static stg_status iteration(stg_gauge *gg, Workspace *ws, int pd, cudaStream_t s, cudaEvent_t *ev)
 {
     const Geom &g = gg->geom;
@@ -212,24 +213,24 @@ static stg_status iteration(stg_gauge *gg, Workspace *ws, int pd, cudaStream_t s
     L.state = ws->state;
     L.partials = ws->partials;
     L.counter = &ws->state->counter;
-    if (ev) STG_CUDA(cudaEventRecord(ev[0], s));
+    if (ev) STG_CUDA(cudaEventRecordWithFlags(ev[0], s, cudaEventRecordExternal));
     // the state flag gates every kernel, including the first half-pass
     L.out_parity = 1;
     L.in = ws->d;
     L.out = t;
     STG_TRY(launch_dslash(g, pd, EPI_GATE, L, s));
-    if (ev) STG_CUDA(cudaEventRecord(ev[1], s));
+    if (ev) STG_CUDA(cudaEventRecordWithFlags(ev[1], s, cudaEventRecordExternal));
     L.out_parity = 0;
     L.in = t;
     L.out = ws->q;
     L.w = ws->d;
     STG_TRY(launch_dslash(g, pd, EPI_A_CG, L, s));
-    if (ev) STG_CUDA(cudaEventRecord(ev[2], s));
+    if (ev) STG_CUDA(cudaEventRecordWithFlags(ev[2], s, cudaEventRecordExternal));
     const int grid = grid_for(g.Vh);
     STG_DISPATCH_PD(pd, k_cg_update, g.Vh, ws->y, ws->r, ws->d, ws->q, ws->state, ws->partials);
-    if (ev) STG_CUDA(cudaEventRecord(ev[3], s));
+    if (ev) STG_CUDA(cudaEventRecordWithFlags(ev[3], s, cudaEventRecordExternal));
     STG_DISPATCH_PD(pd, k_xpay, g.Vh, ws->r, ws->d, ws->state);
-    if (ev) STG_CUDA(cudaEventRecord(ev[4], s));
+    if (ev) STG_CUDA(cudaEventRecordWithFlags(ev[4], s, cudaEventRecordExternal));
     STG_CUDA(cudaGetLastError());
     return STG_OK;
 }
