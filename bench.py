@@ -66,6 +66,21 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", 0)))
 
 
+def max_over_ranks(seconds: float, dist=None, device=None) -> float:
+    """Slowest rank's time (every rank gets it); no collective when alone."""
+    if dist is None:
+        return seconds
+    import torch
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(seconds_max: float, steps: int, world: int) -> float:
+    """Whole-job solves/s: every rank solved `steps` systems of its own."""
+    return world * steps / seconds_max
+
+
 # ---------------------------------------------------------------------------
 # clocks sampled during the timed region
 # ---------------------------------------------------------------------------
@@ -301,12 +316,8 @@ def main():
     ev1.record(stream)
     barrier()
     ck = clocks.stop()
-    elapsed = ev0.elapsed_time(ev1) / 1000.0
-    if dist is not None:
-        t = torch.tensor([elapsed], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
-    value = world * args.steps / elapsed
+    elapsed = max_over_ranks(ev0.elapsed_time(ev1) / 1000.0, dist, dev)
+    value = job_throughput(elapsed, args.steps, world)
     ms_step = 1000.0 * elapsed / args.steps
 
     # true residual of the last solution with the FP64 operator on the GPU
@@ -326,11 +337,7 @@ def main():
         stream.synchronize()
     e1.record(stream)
     barrier()
-    e2e_s = e0.elapsed_time(e1) / 1000.0
-    if dist is not None:
-        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e0.elapsed_time(e1) / 1000.0, dist, dev)
 
     # the GPU's own plain FP64 CG on the same system
     fp64 = None
@@ -403,7 +410,7 @@ def main():
                      "launch_ms_source": tk_source,
                      "gflops_576": vh * 576 / (tk / 1000.0) / 1e9},
         "cpu_baseline": cpu,
-        "e2e": {"value": world * args.steps / e2e_s, "unit": "solves/s",
+        "e2e": {"value": job_throughput(e2e_s, args.steps, world), "unit": "solves/s",
                 "h2d_bytes_per_step": int(b_host.numel() * 16),
                 "d2h_bytes_per_step": int(x_host.numel() * 16)},
         "gpu_launches": int(sum(s["launches"] for s in stats)),
