@@ -197,6 +197,31 @@ stg_status stg_apply_A_dot(const stg_gauge *g, double mass, const void *in_dev,
                            void *out_dev, double *dot_dev, stg_prec prec,
                            stg_stream_t stream);
 
+/*
+ * stg_apply_A_dot without any device allocation.  The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate
+ * device memory -- a latency-bound loop that cannot absorb the device-wide
+ * synchronisation of cudaMalloc / cudaFree, or a host whose device memory is
+ * owned by another allocator or a fixed budget.  It computes exactly what
+ * stg_apply_A_dot computes (same kernels, same summation order), with the
+ * odd intermediate, block partials and counter in a 32 MiB array that the
+ * library reserves statically on every device that loads it (held until the
+ * process exits).
+ *   Arguments as for stg_apply_A_dot; the handle must already exist (its
+ *   links were allocated by stg_gauge_create).
+ *   Limit: 48 Vh (FP64), 24 Vh (FP32) or 16 Vh (FP16) bytes plus 8 bytes per
+ *   256 sites must fit in 32 MiB (FP64 up to 24^3x48, FP32 and FP16 up to
+ *   32^3x64); larger lattices return STG_ERR_INVALID_ARG with a message.
+ *   The first call on a device looks up the array's device address (once per
+ *   device); make that first call before any stream capture.
+ *   All calls on a device share the array: calls whose GPU work overlaps
+ *   (other streams, unordered host threads) race and corrupt each other.
+ *   Calls no cudaMalloc, cudaFree or allocating library routine.
+ */
+stg_status stg_apply_A_dot_noalloc(const stg_gauge *g, double mass, const void *in_dev,
+                                   void *out_dev, double *dot_dev, stg_prec prec,
+                                   stg_stream_t stream);
+
 /* Fill params with the defaults: RELIABLE, sloppy = handle's sloppy
  * precision, delta = 0.1, maxiter = 0 (10 N_dim), check_every = 0 (auto),
  * timing = 0. */

@@ -82,6 +82,7 @@ def _load():
         "stg_dslash": (i, [p, i, p, p, i, p]),
         "stg_apply_A": (i, [p, d, p, p, i, p]),
         "stg_apply_A_dot": (i, [p, d, p, p, p, i, p]),
+        "stg_apply_A_dot_noalloc": (i, [p, d, p, p, p, i, p]),
         "stg_cg_params_default": (i, [p, p]),
         "stg_cg_solve": (i, [p, p, p, d, d, p, p, p]),
     }
@@ -190,6 +191,15 @@ def stg_apply_A_dot(handle: int, mass: float, in_dev, out_dev, dot_dev, prec: in
                     stream=None) -> None:
     _check(lib.stg_apply_A_dot(handle, float(mass), _ptr(in_dev), _ptr(out_dev), _ptr(dot_dev),
                                int(prec), _stream(stream)), "stg_apply_A_dot")
+
+
+def stg_apply_A_dot_noalloc(handle: int, mass: float, in_dev, out_dev, dot_dev, prec: int,
+                            stream=None) -> None:
+    """stg_apply_A_dot for callers that cannot allocate device memory: the
+    scratch is a fixed 32 MiB array reserved by the library on each device."""
+    _check(lib.stg_apply_A_dot_noalloc(handle, float(mass), _ptr(in_dev), _ptr(out_dev),
+                                       _ptr(dot_dev), int(prec), _stream(stream)),
+           "stg_apply_A_dot_noalloc")
 
 
 def stg_cg_params_default(handle: int) -> stg_cg_params:
