@@ -74,7 +74,13 @@ typedef enum stg_status {
     STG_ERR_UNSUPPORTED = 8    /* precision / reconstruction not held by handle */
 } stg_status;
 
-typedef enum stg_prec { STG_FP64 = 0, STG_FP32 = 1, STG_FP16 = 2 } stg_prec;
+/* Storage precision of links and fields.  FP64 and FP32 compute in their own
+ * precision; FP16 (IEEE binary16) and FX16 (16-bit fixed point) store 16-bit
+ * values and compute in FP32.  Fields of both 16-bit kinds carry one FP32
+ * scale per site (the largest |re| or |im| of the site's colour vector);
+ * FX16 links use the fixed scale 1/32767 and so require |U_ab| <= 1, which
+ * holds for SU(3). */
+typedef enum stg_prec { STG_FP64 = 0, STG_FP32 = 1, STG_FP16 = 2, STG_FX16 = 3 } stg_prec;
 
 typedef enum stg_cg_policy {
     STG_CG_RELIABLE = 0, /* Sec. 3.2: Eq. 6 start, reliable + group-wise update */
@@ -91,9 +97,11 @@ typedef struct stg_cg_params {
     long maxiter;      /* bound on the total iteration count (0 = 10 N_dim,
                           N_dim = 3 Vh as in Fig. 1)                           */
     int check_every;   /* inner iterations between host checks (0 = auto)     */
-    int timing;        /* 1: time the four kernels of one inner iteration per
-                          check with CUDA events recorded inside the solver's
-                          graph (stats.t_*); 0: no events                     */
+    int timing;        /* 1: alternate chunks time the four kernels of their
+                          first iteration with CUDA events recorded inside the
+                          solver's graph, and the other chunks whole, with
+                          events around the graph launch (stats.t_*);
+                          0: no events                                         */
 } stg_cg_params;
 
 typedef struct stg_cg_stats {
@@ -109,6 +117,8 @@ typedef struct stg_cg_stats {
     double t_dslash_a_ms;  /* mean duration: q = m^2 d - D_eo t with d^dag q     */
     double t_update_ms;    /* mean duration: y += alpha d, r -= alpha q, |r|^2   */
     double t_xpay_ms;      /* mean duration: d = r + beta d                      */
+    double t_iter_ms;      /* mean duration of one inner iteration, from events
+                              around whole chunks without per-kernel events    */
 } stg_cg_stats;
 
 typedef struct stg_gauge stg_gauge; /* opaque */
@@ -153,14 +163,16 @@ stg_status stg_gauge_dims(const stg_gauge *g, int dims[4], long *vh);
  * Bytes of one checkerboard field (Vh sites, 3 colours) in the device layout
  * of `prec`: FP64 48 Vh (three double2 planes), FP32 24 Vh (float4 plane for
  * colours 0-1, float2 plane for colour 2), FP16 16 Vh (per site three half2
- * colours and one float scale in one 16-byte record).
+ * colours and one float scale in one 16-byte record), FX16 16 Vh (per site
+ * three (re, im) pairs of 16-bit integers q, value q * s, and the float s).
  */
 stg_status stg_field_bytes(const stg_gauge *g, stg_prec prec, size_t *bytes);
 
 /*
  * Convert a canonical complex128 [Vh][3] device field to / from the device
  * layout of `prec` (rounding to nearest on the way down; FP16 stores each
- * site's colour vector divided by its largest |re| or |im| plus that scale).
+ * site's colour vector divided by its largest |re| or |im| plus that scale,
+ * FX16 stores rint(32767 v / max) and max / 32767).
  * Buffers must not overlap.
  */
 stg_status stg_pack_field(const stg_gauge *g, stg_prec prec, const double *canon_dev,
@@ -209,9 +221,9 @@ stg_status stg_apply_A_dot(const stg_gauge *g, double mass, const void *in_dev,
  * process exits).
  *   Arguments as for stg_apply_A_dot; the handle must already exist (its
  *   links were allocated by stg_gauge_create).
- *   Limit: 48 Vh (FP64), 24 Vh (FP32) or 16 Vh (FP16) bytes plus 8 bytes per
- *   256 sites must fit in 32 MiB (FP64 up to 24^3x48, FP32 and FP16 up to
- *   32^3x64); larger lattices return STG_ERR_INVALID_ARG with a message.
+ *   Limit: 48 Vh (FP64), 24 Vh (FP32) or 16 Vh (FP16, FX16) bytes plus 8
+ *   bytes per 256 sites must fit in 32 MiB (FP64 up to 24^3x48, the others
+ *   up to 32^3x64); larger lattices return STG_ERR_INVALID_ARG with a message.
  *   The first call on a device looks up the array's device address (once per
  *   device); make that first call before any stream capture.
  *   All calls on a device share the array: calls whose GPU work overlaps

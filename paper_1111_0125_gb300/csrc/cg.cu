@@ -25,55 +25,104 @@ namespace stg {
 stg_status pack_field(const Geom &g, int prec, const double *canon, void *out, cudaStream_t s);
 stg_status unpack_field(const Geom &g, int prec, const void *in, double *canon, cudaStream_t s);
 
+// one site per thread (setup and update-time kernels)
+int grid_for(long n)
+{
+    long g = (n + kBlock - 1) / kBlock;
+    return (int)(g < 1 ? 1 : g);
+}
+
 static int num_sms()
 {
     static int n = 0;
     if (n == 0) {
         int dev = 0;
         cudaGetDevice(&dev);
-        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+            n = 148;
     }
     return n;
 }
 
-int grid_for(long n)
+// Per-iteration vector kernels: a grid of kVecBlocksPerSM blocks per SM
+// strides over the sites kVecUnroll at a time, issuing every load of the
+// kVecUnroll sites before the first use, so each thread keeps ~300 bytes in
+// flight and each block pays for its reduction barriers once.
+constexpr int kVecBlocksPerSM = 2;
+
+// sites per thread per pass: 4 for FP32 / 16-bit vectors, 2 for FP64 (whose
+// doubled registers would spill at 4)
+__host__ __device__ constexpr int vec_unroll(int pr) { return pr == P64 ? 2 : 4; }
+
+static int grid_vec(long n, int pr)
 {
-    long g = (n + kBlock - 1) / kBlock;
-    long cap = (long)num_sms() * 8;
-    return (int)(g < cap ? (g < 1 ? 1 : g) : cap);
+    const long u = vec_unroll(pr);
+    long g = (n + (long)kBlock * u - 1) / ((long)kBlock * u);
+    long cap = (long)num_sms() * kVecBlocksPerSM;
+    if (g > cap) g = cap;
+    return (int)(g < 1 ? 1 : g);
 }
 
 // ---------------------------------------------------------------------------
 // vector kernels (grid-stride, FP64 reductions)
 // ---------------------------------------------------------------------------
 template <int PD, int PR>
-__global__ void __launch_bounds__(kBlock) k_cg_update(int vh, void *y, void *r, const void *d,
-                                                      const void *q, CGState *st, double *partials)
+__global__ void __launch_bounds__(kBlock, kVecBlocksPerSM)
+k_cg_update(int vh, void *y, void *r, const void *d, const void *q, CGState *st, double *partials)
 {
     if (st->flag != FLAG_RUN) return;
     typedef typename Real<PR>::T T;
+    typedef typename Real<PD>::T TD;
+    constexpr int kVecUnroll = vec_unroll(PR);
     const T alpha = T(st->alpha);
-    double rr = 0.0;
-    for (int i = blockIdx.x * kBlock + threadIdx.x; i < vh; i += gridDim.x * kBlock) {
-        const auto dv = FieldIO<PD>::load(d, vh, i);
-        const auto qv = FieldIO<PD>::load(q, vh, i);
-        Vec3<T> yv = FieldIO<PR>::load(y, vh, i);
-        Vec3<T> rv = FieldIO<PR>::load(r, vh, i);
-        T n = T(0);
+    double rr64 = 0.0;
+    FF rr = {0.f, 0.f};
+    const int stride = gridDim.x * kBlock;
+    for (int base = blockIdx.x * kBlock + threadIdx.x; base < vh; base += kVecUnroll * stride) {
+        Vec3<TD> dv[kVecUnroll], qv[kVecUnroll];
+        Vec3<T> yv[kVecUnroll], rv[kVecUnroll];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            yv.r[c] += alpha * T(dv.r[c]);
-            yv.i[c] += alpha * T(dv.i[c]);
-            rv.r[c] -= alpha * T(qv.r[c]);
-            rv.i[c] -= alpha * T(qv.i[c]);
-            n += rv.r[c] * rv.r[c] + rv.i[c] * rv.i[c];
+        for (int k = 0; k < kVecUnroll; ++k) {
+            const int i = base + k * stride;
+            if (i < vh) {
+                dv[k] = FieldIO<PD>::load(d, vh, i);
+                qv[k] = FieldIO<PD>::load(q, vh, i);
+                yv[k] = FieldIO<PR>::load(y, vh, i);
+                rv[k] = FieldIO<PR>::load(r, vh, i);
+            }
         }
-        FieldIO<PR>::store(y, vh, i, yv);
-        FieldIO<PR>::store(r, vh, i, rv);
-        rr += double(n);
+#pragma unroll
+        for (int k = 0; k < kVecUnroll; ++k) {
+            const int i = base + k * stride;
+            if (i < vh) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    yv[k].r[c] += alpha * T(dv[k].r[c]);
+                    yv[k].i[c] += alpha * T(dv[k].i[c]);
+                    rv[k].r[c] -= alpha * T(qv[k].r[c]);
+                    rv[k].i[c] -= alpha * T(qv[k].i[c]);
+                }
+                FieldIO<PR>::store(y, vh, i, yv[k]);
+                const Vec3<T> rs = FieldIO<PR>::store(r, vh, i, rv[k]);
+                T n = T(0);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) n += rs.r[c] * rs.r[c] + rs.i[c] * rs.i[c];
+                if constexpr (PR == P64) {
+                    rr64 += n;
+                } else {
+                    FF t;
+                    t.hi = float(n);
+                    t.lo = 0.f;
+                    rr = ff_add(rr, t);
+                }
+            }
+        }
     }
     double total;
-    if (grid_sum<kBlock>(rr, partials, &st->counter, total)) {
+    bool last;
+    if constexpr (PR == P64) last = grid_sum<kBlock>(rr64, partials, &st->counter, total);
+    else last = grid_sum_ff<kBlock>(rr, reinterpret_cast<float2 *>(partials), &st->counter, total);
+    if (last) {
         const double old = st->delta_new;
         st->delta_old = old;
         st->delta_new = total;
@@ -88,21 +137,39 @@ __global__ void __launch_bounds__(kBlock) k_cg_update(int vh, void *y, void *r, 
 }
 
 template <int PD, int PR>
-__global__ void __launch_bounds__(kBlock) k_xpay(int vh, const void *r, void *d, const CGState *st)
+__global__ void __launch_bounds__(kBlock, kVecBlocksPerSM)
+k_xpay(int vh, const void *r, void *d, const CGState *st)
 {
     if (st->flag != FLAG_RUN) return;
     typedef typename Real<PR>::T T;
+    typedef typename Real<PD>::T TD;
+    constexpr int kVecUnroll = vec_unroll(PR);
     const T beta = T(st->beta);
-    for (int i = blockIdx.x * kBlock + threadIdx.x; i < vh; i += gridDim.x * kBlock) {
-        const Vec3<T> rv = FieldIO<PR>::load(r, vh, i);
-        const auto dv = FieldIO<PD>::load(d, vh, i);
-        Vec3<typename Real<PD>::T> o;
+    const int stride = gridDim.x * kBlock;
+    for (int base = blockIdx.x * kBlock + threadIdx.x; base < vh; base += kVecUnroll * stride) {
+        Vec3<T> rv[kVecUnroll];
+        Vec3<TD> dv[kVecUnroll];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            o.r[c] = rv.r[c] + beta * T(dv.r[c]);
-            o.i[c] = rv.i[c] + beta * T(dv.i[c]);
+        for (int k = 0; k < kVecUnroll; ++k) {
+            const int i = base + k * stride;
+            if (i < vh) {
+                rv[k] = FieldIO<PR>::load(r, vh, i);
+                dv[k] = FieldIO<PD>::load(d, vh, i);
+            }
         }
-        FieldIO<PD>::store(d, vh, i, o);
+#pragma unroll
+        for (int k = 0; k < kVecUnroll; ++k) {
+            const int i = base + k * stride;
+            if (i < vh) {
+                Vec3<TD> o;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    o.r[c] = rv[k].r[c] + beta * T(dv[k].r[c]);
+                    o.i[c] = rv[k].i[c] + beta * T(dv[k].i[c]);
+                }
+                FieldIO<PD>::store(d, vh, i, o);
+            }
+        }
     }
 }
 
@@ -168,26 +235,41 @@ __global__ void __launch_bounds__(kBlock) k_reset(int vh, void *y, void *r, void
 template <int P>
 __global__ void __launch_bounds__(kBlock) k_norm2(int vh, const void *v, CGState *st, double *partials)
 {
-    double s = 0.0;
+    double s64 = 0.0;
+    FF s = {0.f, 0.f};
     for (int i = blockIdx.x * kBlock + threadIdx.x; i < vh; i += gridDim.x * kBlock) {
         const auto a = FieldIO<P>::load(v, vh, i);
+        if constexpr (P == P64) {
 #pragma unroll
-        for (int c = 0; c < 3; ++c) s += double(a.r[c]) * double(a.r[c]) + double(a.i[c]) * double(a.i[c]);
+            for (int c = 0; c < 3; ++c) s64 += a.r[c] * a.r[c] + a.i[c] * a.i[c];
+        } else {
+            float n = 0.f;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) n += a.r[c] * a.r[c] + a.i[c] * a.i[c];
+            FF t;
+            t.hi = n;
+            t.lo = 0.f;
+            s = ff_add(s, t);
+        }
     }
     double total;
-    if (grid_sum<kBlock>(s, partials, &st->counter, total)) st->result = total;
+    bool last;
+    if constexpr (P == P64) last = grid_sum<kBlock>(s64, partials, &st->counter, total);
+    else last = grid_sum_ff<kBlock>(s, reinterpret_cast<float2 *>(partials), &st->counter, total);
+    if (last) st->result = total;
 }
 
 // ---------------------------------------------------------------------------
 // dispatch over the (PD, PR) pairs used by the solver
 // ---------------------------------------------------------------------------
-static int pr_of(int pd) { return pd == P16 ? P32 : pd; }
+static int pr_of(int pd) { return (pd == P16 || pd == PX16) ? P32 : pd; }
 
 #define STG_DISPATCH_PD(pd, KERNEL, ...)                                                     \
     do {                                                                                     \
         if ((pd) == P64) KERNEL<P64, P64><<<grid, kBlock, 0, s>>>(__VA_ARGS__);              \
         else if ((pd) == P32) KERNEL<P32, P32><<<grid, kBlock, 0, s>>>(__VA_ARGS__);         \
-        else KERNEL<P16, P32><<<grid, kBlock, 0, s>>>(__VA_ARGS__);                          \
+        else if ((pd) == P16) KERNEL<P16, P32><<<grid, kBlock, 0, s>>>(__VA_ARGS__);         \
+        else KERNEL<PX16, P32><<<grid, kBlock, 0, s>>>(__VA_ARGS__);                         \
     } while (0)
 
 static stg_status norm2(const Geom &g, int prec, const void *v, Workspace *ws, cudaStream_t s)
@@ -195,7 +277,8 @@ static stg_status norm2(const Geom &g, int prec, const void *v, Workspace *ws, c
     const int grid = grid_for(g.Vh);
     if (prec == P64) k_norm2<P64><<<grid, kBlock, 0, s>>>(g.Vh, v, ws->state, ws->partials);
     else if (prec == P32) k_norm2<P32><<<grid, kBlock, 0, s>>>(g.Vh, v, ws->state, ws->partials);
-    else k_norm2<P16><<<grid, kBlock, 0, s>>>(g.Vh, v, ws->state, ws->partials);
+    else if (prec == P16) k_norm2<P16><<<grid, kBlock, 0, s>>>(g.Vh, v, ws->state, ws->partials);
+    else k_norm2<PX16><<<grid, kBlock, 0, s>>>(g.Vh, v, ws->state, ws->partials);
     STG_CUDA(cudaGetLastError());
     return STG_OK;
 }
@@ -226,7 +309,7 @@ static stg_status iteration(stg_gauge *gg, Workspace *ws, int pd, cudaStream_t s
     L.w = ws->d;
     STG_TRY(launch_dslash(g, pd, EPI_A_CG, L, s));
     if (ev) STG_CUDA(cudaEventRecordWithFlags(ev[2], s, cudaEventRecordExternal));
-    const int grid = grid_for(g.Vh);
+    const int grid = grid_vec(g.Vh, pr_of(pd));
     STG_DISPATCH_PD(pd, k_cg_update, g.Vh, ws->y, ws->r, ws->d, ws->q, ws->state, ws->partials);
     if (ev) STG_CUDA(cudaEventRecordWithFlags(ev[3], s, cudaEventRecordExternal));
     STG_DISPATCH_PD(pd, k_xpay, g.Vh, ws->r, ws->d, ws->state);
@@ -260,10 +343,11 @@ static stg_status prepare(stg_gauge *g, Workspace *ws, int pd)
         void *v[] = {ws->y, ws->r, ws->d, ws->q};
         for (void *p : v) cudaFree(p);
         ws->y = ws->r = ws->d = ws->q = nullptr;
-        if (ws->graph) {
-            cudaGraphExecDestroy(ws->graph);
-            ws->graph = nullptr;
-        }
+        for (int k = 0; k < 2; ++k)
+            if (ws->graph[k]) {
+                cudaGraphExecDestroy(ws->graph[k]);
+                ws->graph[k] = nullptr;
+            }
         ws->cg_sloppy = pd;
     }
     const int pr = pr_of(pd);
@@ -282,19 +366,20 @@ static stg_status prepare(stg_gauge *g, Workspace *ws, int pd)
 
 // Capture `n` iterations as a graph on a private stream (capture is not
 // allowed on the legacy default stream), replayed on the caller's stream.
-// With timing, the first iteration of the chunk records the 5 events.
-static stg_status get_graph(stg_gauge *g, Workspace *ws, int pd, int n, int timing,
+// The timed variant records the 5 per-kernel events in its first iteration.
+static stg_status get_graph(stg_gauge *g, Workspace *ws, int pd, int n, int timed,
                             cudaGraphExec_t *out)
 {
-    if (ws->graph && ws->graph_sloppy == pd && ws->graph_iters == n && ws->graph_timing == timing) {
-        *out = ws->graph;
+    cudaGraphExec_t &ge = ws->graph[timed];
+    if (ge && ws->graph_sloppy[timed] == pd && ws->graph_iters[timed] == n) {
+        *out = ge;
         return STG_OK;
     }
-    if (ws->graph) {
-        cudaGraphExecDestroy(ws->graph);
-        ws->graph = nullptr;
+    if (ge) {
+        cudaGraphExecDestroy(ge);
+        ge = nullptr;
     }
-    if (timing && !ws->ev[0])
+    if (timed && !ws->ev[0])
         for (int k = 0; k < 5; ++k) STG_CUDA(cudaEventCreate(&ws->ev[k]));
     cudaStream_t cs;
     STG_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
@@ -303,26 +388,25 @@ static stg_status get_graph(stg_gauge *g, Workspace *ws, int pd, int n, int timi
     stg_status st = STG_OK;
     if (e == cudaSuccess) {
         for (int k = 0; k < n && st == STG_OK; ++k)
-            st = iteration(g, ws, pd, cs, (timing && k == 0) ? ws->ev : nullptr);
+            st = iteration(g, ws, pd, cs, (timed && k == 0) ? ws->ev : nullptr);
         cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
         if (st == STG_OK && e2 != cudaSuccess) st = cuda_fail(e2, "cudaStreamEndCapture");
     } else {
         st = cuda_fail(e, "cudaStreamBeginCapture");
     }
     if (st == STG_OK) {
-        e = cudaGraphInstantiate(&ws->graph, graph, 0);
+        e = cudaGraphInstantiate(&ge, graph, 0);
         if (e != cudaSuccess) {
-            ws->graph = nullptr;
+            ge = nullptr;
             st = cuda_fail(e, "cudaGraphInstantiate");
         }
     }
     if (graph) cudaGraphDestroy(graph);
     cudaStreamDestroy(cs);
     if (st != STG_OK) return st;
-    ws->graph_sloppy = pd;
-    ws->graph_iters = n;
-    ws->graph_timing = timing;
-    *out = ws->graph;
+    ws->graph_sloppy[timed] = pd;
+    ws->graph_iters[timed] = n;
+    *out = ge;
     return STG_OK;
 }
 
@@ -382,6 +466,8 @@ stg_status cg_solve(stg_gauge *g, const double *src, double *x, double mass, dou
     if (chunk > 256) chunk = 256;
     long launches = 0;
     double tsum[4] = {0.0, 0.0, 0.0, 0.0};
+    double iter_sum = 0.0;
+    long iter_n = 0;
 
     // b, x0 into the FP64 device layout; |b|^2
     STG_TRY(pack_field(geo, P64, src, ws->b64, s));
@@ -433,11 +519,27 @@ stg_status cg_solve(stg_gauge *g, const double *src, double *x, double mass, dou
         h->track_max = (p->policy == STG_CG_RELIABLE) ? 1 : 0;
         h->counter = 0;
         if (status == STG_OK) status = write_state(ws, s);
-        cudaGraphExec_t graph = nullptr;
-        if (status == STG_OK) status = get_graph(g, ws, pd, chunk, p->timing ? 1 : 0, &graph);
+        cudaGraphExec_t graph = nullptr, graph_timed = nullptr;
+        if (status == STG_OK) status = get_graph(g, ws, pd, chunk, 0, &graph);
+        if (status == STG_OK && p->timing) status = get_graph(g, ws, pd, chunk, 1, &graph_timed);
+        if (status == STG_OK && p->timing && !ws->ev_chunk[0]) {
+            for (int k = 0; k < 2 && status == STG_OK; ++k) {
+                cudaError_t e = cudaEventCreate(&ws->ev_chunk[k]);
+                if (e != cudaSuccess) status = cuda_fail(e, "cudaEventCreate");
+            }
+        }
         int breakdowns = 0;
+        long chunk_no = 0;
         while (status == STG_OK) {
-            cudaError_t e = cudaGraphLaunch(graph, s);
+            // with timing, chunks alternate: per-kernel events in even chunks,
+            // events around the whole launch of odd (plain) chunks
+            const bool kernel_timed = p->timing && (chunk_no % 2 == 0);
+            const bool chunk_timed = p->timing && !kernel_timed;
+            ++chunk_no;
+            cudaError_t e = cudaSuccess;
+            if (chunk_timed) e = cudaEventRecord(ws->ev_chunk[0], s);
+            if (e == cudaSuccess) e = cudaGraphLaunch(kernel_timed ? graph_timed : graph, s);
+            if (e == cudaSuccess && chunk_timed) e = cudaEventRecord(ws->ev_chunk[1], s);
             if (e != cudaSuccess) {
                 status = cuda_fail(e, "cudaGraphLaunch");
                 break;
@@ -445,7 +547,17 @@ stg_status cg_solve(stg_gauge *g, const double *src, double *x, double mass, dou
             status = read_state(ws, s);
             if (status != STG_OK) break;
             launches += 4L * chunk;
-            if (p->timing) {
+            if (chunk_timed && h->flag == FLAG_RUN) {
+                // every iteration of the chunk ran in full
+                float ms = 0.f;
+                if (cudaEventElapsedTime(&ms, ws->ev_chunk[0], ws->ev_chunk[1]) == cudaSuccess) {
+                    iter_sum += ms / chunk;
+                    ++iter_n;
+                } else {
+                    cudaGetLastError();
+                }
+            }
+            if (kernel_timed) {
                 // the chunk's first iteration always runs: a chunk starts with the flag down
                 float ms[4];
                 bool ok = true;
@@ -518,6 +630,7 @@ stg_status cg_solve(stg_gauge *g, const double *src, double *x, double mass, dou
         st.t_update_ms = tsum[2] / st.timed_iters;
         st.t_xpay_ms = tsum[3] / st.timed_iters;
     }
+    if (iter_n > 0) st.t_iter_ms = iter_sum / iter_n;
     // setup: 2 packs, norm, residual (2), reset; per update: accumulate,
     // residual (2), reset; final unpack
     launches += 6 + 4L * st.updates + 1;

@@ -11,6 +11,9 @@
 // FP32/12), so there are no tensor cores here: the 3x3 complex mat-vecs run
 // on the FP32 / FP64 pipes in registers.
 //
+// Reductions of FP64 data sum in FP64; those of FP32 / 16-bit data use the
+// compensated FP32 pairs of grid_sum_ff (the FP64 pipe is ~1/64 of FP32 here).
+//
 // Epilogues (all fused into the second half-pass of A, Eq. 3):
 //   EPI_NONE  out = D in
 //   EPI_GATE  out = D in, skipped when the CG state flag is raised
@@ -22,22 +25,6 @@
 
 namespace stg {
 
-struct DslashArgs {
-    Geom g;
-    const char *lf[4];  // forward link blocks  (parity p,   mu)
-    const char *lb[4];  // backward link blocks (parity 1-p, mu)
-    int parity;
-    const void *in;
-    void *out;
-    const void *w;
-    const void *v;
-    double m2;
-    double *dot;
-    CGState *state;
-    double *partials;
-    unsigned *counter;
-};
-
 template <int P, int R, int EPI>
 __global__ void __launch_bounds__(kBlock) k_dslash(const DslashArgs a)
 {
@@ -47,7 +34,7 @@ __global__ void __launch_bounds__(kBlock) k_dslash(const DslashArgs a)
     }
     const int i = blockIdx.x * kBlock + threadIdx.x;
     const int vh = a.g.Vh;
-    double dot = 0.0;
+    T dot = T(0);
     if (i < vh) {
         const Site s = site_of(a.g, i, a.parity);
         Vec3<T> acc;
@@ -59,12 +46,21 @@ __global__ void __launch_bounds__(kBlock) k_dslash(const DslashArgs a)
             neighbours(a.g, s, i, mu, jf, jb);
             float sf = 1.f, sb = 1.f;
             if (R == 12) link_signs(a.g, s, mu, sf, sb);
-            const Mat3<T> uf = LinkIO<P, R>::load(a.lf[mu], vh, i, T(sf));
+            const T s2f = (R == 12) ? T(sf * LinkPost<P>::row2) : T(1);
+            const T s2b = (R == 12) ? T(sb * LinkPost<P>::row2) : T(1);
+            const Mat3<T> uf = LinkIO<P, R>::load(a.lf[mu], vh, i);
             const Vec3<T> vf = FieldIO<P>::load_nc(a.in, vh, jf);
-            mul_add(uf, vf, acc);
-            const Mat3<T> ub = LinkIO<P, R>::load(a.lb[mu], vh, jb, T(sb));
+            mul_add(uf, vf, acc, s2f);
+            const Mat3<T> ub = LinkIO<P, R>::load(a.lb[mu], vh, jb);
             const Vec3<T> vb = FieldIO<P>::load_nc(a.in, vh, jb);
-            adj_mul_sub(ub, vb, acc);
+            adj_mul_sub(ub, vb, acc, s2b);
+        }
+        if (P == PX16) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                acc.r[c] *= T(LinkPost<PX16>::k);
+                acc.i[c] *= T(LinkPost<PX16>::k);
+            }
         }
         if (EPI == EPI_NONE || EPI == EPI_GATE) {
             FieldIO<P>::store(a.out, vh, i, acc);
@@ -73,33 +69,41 @@ __global__ void __launch_bounds__(kBlock) k_dslash(const DslashArgs a)
             const Vec3<T> x = FieldIO<P>::load_nc(a.v, vh, i);
             const T m2 = T(a.m2);
             Vec3<T> o;
-            T nr = T(0);
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 o.r[c] = b.r[c] - m2 * x.r[c] + acc.r[c];
                 o.i[c] = b.i[c] - m2 * x.i[c] + acc.i[c];
-                nr += o.r[c] * o.r[c] + o.i[c] * o.i[c];
             }
-            FieldIO<P>::store(a.out, vh, i, o);
-            dot = double(nr);
+            const Vec3<T> os = FieldIO<P>::store(a.out, vh, i, o);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) dot += os.r[c] * os.r[c] + os.i[c] * os.i[c];
         } else {
             const T m2 = (EPI == EPI_A_CG) ? T(a.state->m2) : T(a.m2);
             const Vec3<T> d = FieldIO<P>::load_nc(a.w, vh, i);
             Vec3<T> o;
-            T dq = T(0);
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 o.r[c] = m2 * d.r[c] - acc.r[c];
                 o.i[c] = m2 * d.i[c] - acc.i[c];
-                dq += d.r[c] * o.r[c] + d.i[c] * o.i[c];
             }
-            FieldIO<P>::store(a.out, vh, i, o);
-            dot = double(dq);
+            // d^dag q with q as stored, i.e. as the CG update will read it
+            const Vec3<T> os = FieldIO<P>::store(a.out, vh, i, o);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) dot += d.r[c] * os.r[c] + d.i[c] * os.i[c];
         }
     }
     if (EPI == EPI_A_DOT || EPI == EPI_A_CG || EPI == EPI_RES) {
         double total;
-        if (grid_sum<kBlock>(dot, a.partials, a.counter, total)) {
+        bool last;
+        if constexpr (P == P64) {
+            last = grid_sum<kBlock>(double(dot), a.partials, a.counter, total);
+        } else {
+            FF v;
+            v.hi = float(dot);
+            v.lo = 0.f;
+            last = grid_sum_ff<kBlock>(v, reinterpret_cast<float2 *>(a.partials), a.counter, total);
+        }
+        if (last) {
             if (EPI == EPI_A_CG) {
                 CGState *st = a.state;
                 st->pAp = total;
@@ -148,6 +152,11 @@ stg_status launch_dslash(const Geom &g, int prec, int epi, const DslashLaunch &L
     if (prec != L.links->prec) {
         set_error("dslash: link precision does not match the field precision");
         return STG_ERR_UNSUPPORTED;
+    }
+    if (prec == PX16) {  // two sites per thread on packed FP32x2 (dslash_fx16.cu)
+        launch_dslash_fx2(recon, epi, a, s);
+        STG_CUDA(cudaGetLastError());
+        return STG_OK;
     }
     if (prec == P64) {
         if (recon == 18) launch_pr<P64, 18>(epi, a, grid, s);

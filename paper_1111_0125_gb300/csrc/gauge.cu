@@ -24,6 +24,9 @@ Geom make_geom(const int dims[4])
     g.sy = g.Lxh;
     g.sz = g.Lxh * dims[1];
     g.st = g.Lxh * dims[1] * dims[2];
+    g.dxh = make_fastdiv((unsigned)g.Lxh);
+    g.dy = make_fastdiv((unsigned)dims[1]);
+    g.dz = make_fastdiv((unsigned)dims[2]);
     return g;
 }
 
@@ -72,6 +75,30 @@ __global__ void k_pack_links(Geom g, const double2 *__restrict__ ucan, char *bas
                                                 (float)u[2 * q + 1].x, (float)u[2 * q + 1].y);
         if (R == 18)
             reinterpret_cast<float2 *>(p + (size_t)4 * vh)[i] = make_float2((float)u[8].x, (float)u[8].y);
+    } else if (P == PX16) {
+        // entries of a unitary link are bounded by 1: q = rint(32767 U), no scale
+        const float k = 32767.0f;
+        uint4 *p = reinterpret_cast<uint4 *>(blk);
+        uint4 a;
+        a.x = fx_pack(k * (float)u[0].x, k * (float)u[0].y);
+        a.y = fx_pack(k * (float)u[1].x, k * (float)u[1].y);
+        a.z = fx_pack(k * (float)u[2].x, k * (float)u[2].y);
+        a.w = fx_pack(k * (float)u[3].x, k * (float)u[3].y);
+        p[i] = a;
+        if (R == 18) {
+            uint4 b;
+            b.x = fx_pack(k * (float)u[4].x, k * (float)u[4].y);
+            b.y = fx_pack(k * (float)u[5].x, k * (float)u[5].y);
+            b.z = fx_pack(k * (float)u[6].x, k * (float)u[6].y);
+            b.w = fx_pack(k * (float)u[7].x, k * (float)u[7].y);
+            p[(size_t)vh + i] = b;
+            reinterpret_cast<unsigned *>(p + (size_t)2 * vh)[i] = fx_pack(k * (float)u[8].x, k * (float)u[8].y);
+        } else {
+            uint2 b;
+            b.x = fx_pack(k * (float)u[4].x, k * (float)u[4].y);
+            b.y = fx_pack(k * (float)u[5].x, k * (float)u[5].y);
+            reinterpret_cast<uint2 *>(p + (size_t)vh)[i] = b;
+        }
     } else {
         uint4 *p = reinterpret_cast<uint4 *>(blk);
         uint4 a;
@@ -114,7 +141,8 @@ static stg_status pack_links(const Geom &g, const double2 *ucan, int prec, int r
 #define STG_PACK(P_, R_) k_pack_links<P_, R_><<<grid, 256, 0, s>>>(g, ucan, lf->base, lf->blk_bytes)
     if (prec == P64) { if (recon == 18) STG_PACK(P64, 18); else STG_PACK(P64, 12); }
     else if (prec == P32) { if (recon == 18) STG_PACK(P32, 18); else STG_PACK(P32, 12); }
-    else { if (recon == 18) STG_PACK(P16, 18); else STG_PACK(P16, 12); }
+    else if (prec == P16) { if (recon == 18) STG_PACK(P16, 18); else STG_PACK(P16, 12); }
+    else { if (recon == 18) STG_PACK(PX16, 18); else STG_PACK(PX16, 12); }
 #undef STG_PACK
     STG_CUDA(cudaGetLastError());
     return STG_OK;
@@ -155,7 +183,8 @@ stg_status pack_field(const Geom &g, int prec, const double *canon, void *out, c
     const double2 *c = reinterpret_cast<const double2 *>(canon);
     if (prec == P64) k_pack_field<P64><<<grid, 256, 0, s>>>(g.Vh, c, out);
     else if (prec == P32) k_pack_field<P32><<<grid, 256, 0, s>>>(g.Vh, c, out);
-    else k_pack_field<P16><<<grid, 256, 0, s>>>(g.Vh, c, out);
+    else if (prec == P16) k_pack_field<P16><<<grid, 256, 0, s>>>(g.Vh, c, out);
+    else k_pack_field<PX16><<<grid, 256, 0, s>>>(g.Vh, c, out);
     STG_CUDA(cudaGetLastError());
     return STG_OK;
 }
@@ -166,7 +195,8 @@ stg_status unpack_field(const Geom &g, int prec, const void *in, double *canon, 
     double2 *c = reinterpret_cast<double2 *>(canon);
     if (prec == P64) k_unpack_field<P64><<<grid, 256, 0, s>>>(g.Vh, in, c);
     else if (prec == P32) k_unpack_field<P32><<<grid, 256, 0, s>>>(g.Vh, in, c);
-    else k_unpack_field<P16><<<grid, 256, 0, s>>>(g.Vh, in, c);
+    else if (prec == P16) k_unpack_field<P16><<<grid, 256, 0, s>>>(g.Vh, in, c);
+    else k_unpack_field<PX16><<<grid, 256, 0, s>>>(g.Vh, in, c);
     STG_CUDA(cudaGetLastError());
     return STG_OK;
 }
@@ -287,13 +317,16 @@ stg_status workspace_tmp(stg_gauge *g, int prec, void **out)
 void workspace_free(Workspace *ws)
 {
     if (!ws) return;
-    if (ws->graph) cudaGraphExecDestroy(ws->graph);
+    for (int k = 0; k < 2; ++k)
+        if (ws->graph[k]) cudaGraphExecDestroy(ws->graph[k]);
     for (int k = 0; k < 5; ++k)
         if (ws->ev[k]) cudaEventDestroy(ws->ev[k]);
+    for (int k = 0; k < 2; ++k)
+        if (ws->ev_chunk[k]) cudaEventDestroy(ws->ev_chunk[k]);
     cudaFree(ws->partials);
     cudaFree(ws->state);
     if (ws->state_host) cudaFreeHost(ws->state_host);
-    for (int p = 0; p < 3; ++p) cudaFree(ws->tmp[p]);
+    for (int p = 0; p < 4; ++p) cudaFree(ws->tmp[p]);
     void *v[] = {ws->x64, ws->b64, ws->r64, ws->t64, ws->y, ws->r, ws->d, ws->q};
     for (void *p : v) cudaFree(p);
     delete ws;

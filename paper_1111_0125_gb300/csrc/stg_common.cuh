@@ -10,7 +10,9 @@
 
 namespace stg {
 
-enum Prec { P64 = 0, P32 = 1, P16 = 2 };
+// P16: IEEE binary16 storage; PX16: 16-bit fixed point (int16 with a per-
+// site FP32 scale for fields, a fixed 1/32767 for links).  Both compute in FP32.
+enum Prec { P64 = 0, P32 = 1, P16 = 2, PX16 = 3 };
 
 // ---------------------------------------------------------------------------
 // Geometry.  Site (x, y, z, t), lex = x + Lx (y + Ly (z + Lz t)), parity
@@ -18,11 +20,44 @@ enum Prec { P64 = 0, P32 = 1, P16 = 2 };
 // parity the y, z and t neighbours are at i +- sy, sz, st; the x neighbour
 // keeps the row (i - x/2) and moves x/2 by the parity-dependent hop.
 // ---------------------------------------------------------------------------
+// Division by a runtime constant d through a multiply-high (the round-up
+// method of Granlund and Montgomery): for n < 2^31,
+//   n / d = (umulhi(n, m) + n) >> s,  s = ceil(log2 d),
+//   m = floor(2^32 (2^s - d) / d) + 1   (m = s = 0 for d = 1).
+struct FastDiv {
+    unsigned d, m, s;
+    __host__ __device__ __forceinline__ unsigned div(unsigned n) const
+    {
+#ifdef __CUDA_ARCH__
+        return (__umulhi(n, m) + n) >> s;
+#else
+        return (unsigned)(((unsigned long long)n * m >> 32) + n) >> s;
+#endif
+    }
+};
+
+inline FastDiv make_fastdiv(unsigned d)
+{
+    FastDiv f;
+    f.d = d;
+    if (d <= 1) {
+        f.m = 0;
+        f.s = 0;
+        return f;
+    }
+    unsigned l = 0;
+    while ((1ull << l) < d) ++l;
+    f.s = l;
+    f.m = (unsigned)(((1ull << 32) * ((1ull << l) - d)) / d + 1);
+    return f;
+}
+
 struct Geom {
     int L[4];  // Lx, Ly, Lz, Lt
     int Lxh;   // Lx / 2
     int Vh;    // sites per parity
     int sy, sz, st;
+    FastDiv dxh, dy, dz;  // division by Lx/2, Ly, Lz
 };
 
 struct Site {
@@ -33,13 +68,13 @@ struct Site {
 __device__ __forceinline__ Site site_of(const Geom &g, int i, int parity)
 {
     Site s;
-    int xh = i % g.Lxh;
-    int r = i / g.Lxh;
-    s.row = i - xh;
-    s.y = r % g.L[1];
-    r /= g.L[1];
-    s.z = r % g.L[2];
-    s.t = r / g.L[2];
+    const int r = (int)g.dxh.div((unsigned)i);
+    s.row = r * g.Lxh;
+    const int xh = i - s.row;
+    const int r2 = (int)g.dy.div((unsigned)r);
+    s.y = r - r2 * g.L[1];
+    s.t = (int)g.dz.div((unsigned)r2);
+    s.z = r2 - s.t * g.L[2];
     s.x = 2 * xh + ((parity + s.y + s.z + s.t) & 1);
     return s;
 }
@@ -92,7 +127,7 @@ template <> struct Real<P64> { typedef double T; };
 // Bytes per site of one checkerboard field in the device layout.
 __host__ __device__ constexpr int field_site_bytes(int p)
 {
-    return p == P64 ? 48 : (p == P32 ? 24 : 16);
+    return p == P64 ? 48 : (p == P32 ? 24 : 16);  // P16 and PX16: 16
 }
 
 // Bytes of one link in the device layout.
@@ -100,7 +135,7 @@ __host__ __device__ constexpr int link_bytes(int p, int recon)
 {
     return p == P64 ? (recon == 18 ? 144 : 96)
          : p == P32 ? (recon == 18 ? 72 : 48)
-                    : (recon == 18 ? 36 : 24);
+                    : (recon == 18 ? 36 : 24);  // P16 and PX16
 }
 
 // ---------------------------------------------------------------------------
@@ -141,11 +176,13 @@ template <> struct FieldIO<P64> {
     {
         return load<true>(f, vh, s);
     }
-    __device__ __forceinline__ static void store(void *f, int vh, int s, const Vec3<double> &v)
+    // store returns the value as a later load will see it
+    __device__ __forceinline__ static Vec3<double> store(void *f, int vh, int s, const Vec3<double> &v)
     {
         double2 *p = static_cast<double2 *>(f);
 #pragma unroll
         for (int c = 0; c < 3; ++c) p[(size_t)c * vh + s] = make_double2(v.r[c], v.i[c]);
+        return v;
     }
 };
 
@@ -167,12 +204,13 @@ template <> struct FieldIO<P32> {
     {
         return load<true>(f, vh, s);
     }
-    __device__ __forceinline__ static void store(void *f, int vh, int s, const Vec3<float> &v)
+    __device__ __forceinline__ static Vec3<float> store(void *f, int vh, int s, const Vec3<float> &v)
     {
         float4 *p4 = static_cast<float4 *>(f);
         float2 *p2 = reinterpret_cast<float2 *>(p4 + vh);
         p4[s] = make_float4(v.r[0], v.i[0], v.r[1], v.i[1]);
         p2[s] = make_float2(v.r[2], v.i[2]);
+        return v;
     }
 };
 
@@ -205,7 +243,7 @@ template <> struct FieldIO<P16> {
     {
         return load<true>(f, vh, s);
     }
-    __device__ __forceinline__ static void store(void *f, int vh, int s, const Vec3<float> &v)
+    __device__ __forceinline__ static Vec3<float> store(void *f, int vh, int s, const Vec3<float> &v)
     {
         float m = 0.f;
 #pragma unroll
@@ -217,6 +255,75 @@ template <> struct FieldIO<P16> {
         u.z = f2_to_h2(v.r[2] * inv, v.i[2] * inv);
         u.w = __float_as_uint(m);
         static_cast<uint4 *>(f)[s] = u;
+        float2 a = h2_to_f2(u.x), b = h2_to_f2(u.y), c = h2_to_f2(u.z);
+        Vec3<float> o;
+        o.r[0] = a.x * m; o.i[0] = a.y * m;
+        o.r[1] = b.x * m; o.i[1] = b.y * m;
+        o.r[2] = c.x * m; o.i[2] = c.y * m;
+        return o;
+    }
+};
+
+// 16-bit fixed point: a component q in [-32767, 32767] is kept as the
+// unsigned offset u = q + 32768.  Decoding puts u into the low mantissa bits
+// of 1.5 * 2^23 (one byte permute) and subtracts 1.5 * 2^23 + 32768, which
+// is exact in FP32.
+__device__ __forceinline__ float fx_lo(unsigned w)
+{
+    return __int_as_float((int)__byte_perm(w, 0x4B40u, 0x5410)) - 12615680.0f;
+}
+__device__ __forceinline__ float fx_hi(unsigned w)
+{
+    return __int_as_float((int)__byte_perm(w, 0x4B40u, 0x5432)) - 12615680.0f;
+}
+// Encoding: x (already scaled to [-32767, 32767]) plus 1.5 * 2^23 + 32768
+// rounds to the nearest integer in FP32, leaving rint(x) + 32768 in the low
+// 16 bits; one byte permute packs the (re, im) pair.
+__device__ __forceinline__ unsigned fx_pack(float re, float im)
+{
+    re = fminf(fmaxf(re, -32767.f), 32767.f);
+    im = fminf(fmaxf(im, -32767.f), 32767.f);
+    const unsigned a = __float_as_uint(re + 12615680.0f);
+    const unsigned b = __float_as_uint(im + 12615680.0f);
+    return __byte_perm(a, b, 0x5410);
+}
+
+// PX16 field: one 16-byte record {3 words of (re, im) fixed point, f32 s}
+// with value = q * s and s = max |component| / 32767 of the site.
+template <> struct FieldIO<PX16> {
+    template <bool NC = false>
+    __device__ __forceinline__ static Vec3<float> load(const void *f, int vh, int s)
+    {
+        uint4 u = ld<uint4, NC>(static_cast<const uint4 *>(f) + s);
+        const float sc = __uint_as_float(u.w);
+        Vec3<float> v;
+        v.r[0] = fx_lo(u.x) * sc; v.i[0] = fx_hi(u.x) * sc;
+        v.r[1] = fx_lo(u.y) * sc; v.i[1] = fx_hi(u.y) * sc;
+        v.r[2] = fx_lo(u.z) * sc; v.i[2] = fx_hi(u.z) * sc;
+        return v;
+    }
+    __device__ __forceinline__ static Vec3<float> load_nc(const void *f, int vh, int s)
+    {
+        return load<true>(f, vh, s);
+    }
+    __device__ __forceinline__ static Vec3<float> store(void *f, int vh, int s, const Vec3<float> &v)
+    {
+        float m = 0.f;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) m = fmaxf(m, fmaxf(fabsf(v.r[c]), fabsf(v.i[c])));
+        const float k = m > 0.f ? 32767.0f / m : 0.f;
+        const float sc = m * (1.0f / 32767.0f);
+        uint4 u;
+        u.x = fx_pack(v.r[0] * k, v.i[0] * k);
+        u.y = fx_pack(v.r[1] * k, v.i[1] * k);
+        u.z = fx_pack(v.r[2] * k, v.i[2] * k);
+        u.w = __float_as_uint(sc);
+        static_cast<uint4 *>(f)[s] = u;
+        Vec3<float> o;
+        o.r[0] = fx_lo(u.x) * sc; o.i[0] = fx_hi(u.x) * sc;
+        o.r[1] = fx_lo(u.y) * sc; o.i[1] = fx_hi(u.y) * sc;
+        o.r[2] = fx_lo(u.z) * sc; o.i[2] = fx_hi(u.z) * sc;
+        return o;
     }
 };
 
@@ -227,8 +334,9 @@ template <> struct FieldIO<P16> {
 //   P32/12: 3 float4 planes (00,01)(02,10)(11,12)
 //   P16/18: 2 uint4 planes of 4 half2 + one 4-byte half2 plane (22)
 //   P16/12: 1 uint4 plane (00,01,02,10) + one uint2 plane (11,12)
-// For recon 12 row 2 = s * conj(row0 x row1), s = the folded phase of the
-// link (s U is stored; det(s U) = s for U in SU(3)).
+// For recon 12 the loader returns row 2 = conj(row0 x row1); the true row 2
+// of the stored s U is s times that (det(s U) = s for U in SU(3)), and the
+// mat-vecs apply s (times 1/32767 for PX16) to row 2's contribution.
 // ---------------------------------------------------------------------------
 template <typename T> struct Mat3 {
     T r[3][3], i[3][3];
@@ -257,102 +365,199 @@ __device__ __forceinline__ void reconstruct_row2(Mat3<T> &u, T s)
     }
 }
 
+// Link loads: every link is read exactly once per half-pass, so they bypass
+// L1 (no_allocate) and leave it to the neighbour colour vectors, which are
+// read eight times each.
+__device__ __forceinline__ uint4 ld_stream(const uint4 *p)
+{
+    uint4 v;
+    asm("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ uint2 ld_stream(const uint2 *p)
+{
+    uint2 v;
+    asm("ld.global.nc.L1::no_allocate.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ unsigned ld_stream(const unsigned *p)
+{
+    unsigned v;
+    asm("ld.global.nc.L1::no_allocate.u32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ float4 ld_stream(const float4 *p)
+{
+    float4 v;
+    asm("ld.global.nc.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ float2 ld_stream(const float2 *p)
+{
+    float2 v;
+    asm("ld.global.nc.L1::no_allocate.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ double2 ld_stream(const double2 *p)
+{
+    double2 v;
+    asm("ld.global.nc.L1::no_allocate.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "l"(p));
+    return v;
+}
+
 template <int P, int R> struct LinkIO;
 
 template <int R> struct LinkIO<P64, R> {
-    __device__ __forceinline__ static Mat3<double> load(const char *blk, int vh, int s, double sign)
+    __device__ __forceinline__ static Mat3<double> load(const char *blk, int vh, int s)
     {
         const double2 *p = reinterpret_cast<const double2 *>(blk);
         Mat3<double> u;
         constexpr int n = R == 18 ? 9 : 6;
 #pragma unroll
         for (int k = 0; k < n; ++k) {
-            double2 a = __ldg(p + (size_t)k * vh + s);
+            double2 a = ld_stream(p + (size_t)k * vh + s);
             set_entry(u, k, a.x, a.y);
         }
-        if (R == 12) reconstruct_row2(u, sign);
+        if (R == 12) reconstruct_row2(u, 1.0);
         return u;
     }
 };
 
 template <int R> struct LinkIO<P32, R> {
-    __device__ __forceinline__ static Mat3<float> load(const char *blk, int vh, int s, float sign)
+    __device__ __forceinline__ static Mat3<float> load(const char *blk, int vh, int s)
     {
         const float4 *p = reinterpret_cast<const float4 *>(blk);
         Mat3<float> u;
         constexpr int n4 = R == 18 ? 4 : 3;
 #pragma unroll
         for (int k = 0; k < n4; ++k) {
-            float4 a = __ldg(p + (size_t)k * vh + s);
+            float4 a = ld_stream(p + (size_t)k * vh + s);
             set_entry(u, 2 * k, a.x, a.y);
             set_entry(u, 2 * k + 1, a.z, a.w);
         }
         if (R == 18) {
-            float2 b = __ldg(reinterpret_cast<const float2 *>(p + (size_t)4 * vh) + s);
+            float2 b = ld_stream(reinterpret_cast<const float2 *>(p + (size_t)4 * vh) + s);
             set_entry(u, 8, b.x, b.y);
         } else {
-            reconstruct_row2(u, sign);
+            reconstruct_row2(u, 1.0f);
         }
         return u;
     }
 };
 
 template <int R> struct LinkIO<P16, R> {
-    __device__ __forceinline__ static Mat3<float> load(const char *blk, int vh, int s, float sign)
+    __device__ __forceinline__ static Mat3<float> load(const char *blk, int vh, int s)
     {
         const uint4 *p = reinterpret_cast<const uint4 *>(blk);
         Mat3<float> u;
-        uint4 a = __ldg(p + s);
+        uint4 a = ld_stream(p + s);
         float2 e0 = h2_to_f2(a.x), e1 = h2_to_f2(a.y), e2 = h2_to_f2(a.z), e3 = h2_to_f2(a.w);
         set_entry(u, 0, e0.x, e0.y);
         set_entry(u, 1, e1.x, e1.y);
         set_entry(u, 2, e2.x, e2.y);
         set_entry(u, 3, e3.x, e3.y);
         if (R == 18) {
-            uint4 b = __ldg(p + (size_t)vh + s);
+            uint4 b = ld_stream(p + (size_t)vh + s);
             float2 f0 = h2_to_f2(b.x), f1 = h2_to_f2(b.y), f2 = h2_to_f2(b.z), f3 = h2_to_f2(b.w);
             set_entry(u, 4, f0.x, f0.y);
             set_entry(u, 5, f1.x, f1.y);
             set_entry(u, 6, f2.x, f2.y);
             set_entry(u, 7, f3.x, f3.y);
-            unsigned c = __ldg(reinterpret_cast<const unsigned *>(p + (size_t)2 * vh) + s);
+            unsigned c = ld_stream(reinterpret_cast<const unsigned *>(p + (size_t)2 * vh) + s);
             float2 g = h2_to_f2(c);
             set_entry(u, 8, g.x, g.y);
         } else {
-            uint2 b = __ldg(reinterpret_cast<const uint2 *>(p + (size_t)vh) + s);
+            uint2 b = ld_stream(reinterpret_cast<const uint2 *>(p + (size_t)vh) + s);
             float2 f0 = h2_to_f2(b.x), f1 = h2_to_f2(b.y);
             set_entry(u, 4, f0.x, f0.y);
             set_entry(u, 5, f1.x, f1.y);
-            reconstruct_row2(u, sign);
+            reconstruct_row2(u, 1.0f);
         }
         return u;
     }
 };
 
-// acc += U v
+// PX16 links: entries q = rint(32767 U_ab) as offsets, no per-link scale.
+// load returns 32767 * U (integer-valued floats); the kernel multiplies its
+// accumulated sum by 1/32767 once per site (LinkPost).  Row 2 of a 12-real
+// link is s conj(r0 x r1) / 32767, which keeps it on the same 32767 scale.
+template <int R> struct LinkIO<PX16, R> {
+    __device__ __forceinline__ static Mat3<float> load(const char *blk, int vh, int s)
+    {
+        const uint4 *p = reinterpret_cast<const uint4 *>(blk);
+        Mat3<float> u;
+        uint4 a = ld_stream(p + s);
+        set_entry(u, 0, fx_lo(a.x), fx_hi(a.x));
+        set_entry(u, 1, fx_lo(a.y), fx_hi(a.y));
+        set_entry(u, 2, fx_lo(a.z), fx_hi(a.z));
+        set_entry(u, 3, fx_lo(a.w), fx_hi(a.w));
+        if (R == 18) {
+            uint4 b = ld_stream(p + (size_t)vh + s);
+            set_entry(u, 4, fx_lo(b.x), fx_hi(b.x));
+            set_entry(u, 5, fx_lo(b.y), fx_hi(b.y));
+            set_entry(u, 6, fx_lo(b.z), fx_hi(b.z));
+            set_entry(u, 7, fx_lo(b.w), fx_hi(b.w));
+            unsigned c = ld_stream(reinterpret_cast<const unsigned *>(p + (size_t)2 * vh) + s);
+            set_entry(u, 8, fx_lo(c), fx_hi(c));
+        } else {
+            uint2 b = ld_stream(reinterpret_cast<const uint2 *>(p + (size_t)vh) + s);
+            set_entry(u, 4, fx_lo(b.x), fx_hi(b.x));
+            set_entry(u, 5, fx_lo(b.y), fx_hi(b.y));
+            reconstruct_row2(u, 1.0f);
+        }
+        return u;
+    }
+};
+
+// factor applied to the accumulated D chi of a site (1/32767 for PX16 links)
+// and, for 12-real links, the extra factor of row 2's contribution
+template <int P> struct LinkPost {
+    static constexpr float k = 1.0f;
+    static constexpr float row2 = 1.0f;
+};
+template <> struct LinkPost<PX16> {
+    static constexpr float k = 1.0f / 32767.0f;
+    static constexpr float row2 = 1.0f / 32767.0f;
+};
+
+// acc += U v, with row 2 of U scaled by s2 (the 12-real sign; 1 for 18-real)
 template <typename T>
-__device__ __forceinline__ void mul_add(const Mat3<T> &u, const Vec3<T> &v, Vec3<T> &acc)
+__device__ __forceinline__ void mul_add(const Mat3<T> &u, const Vec3<T> &v, Vec3<T> &acc, T s2)
 {
 #pragma unroll
-    for (int a = 0; a < 3; ++a)
+    for (int a = 0; a < 2; ++a)
 #pragma unroll
         for (int b = 0; b < 3; ++b) {
             acc.r[a] += u.r[a][b] * v.r[b] - u.i[a][b] * v.i[b];
             acc.i[a] += u.r[a][b] * v.i[b] + u.i[a][b] * v.r[b];
         }
+    T wr = T(0), wi = T(0);
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        wr += u.r[2][b] * v.r[b] - u.i[2][b] * v.i[b];
+        wi += u.r[2][b] * v.i[b] + u.i[2][b] * v.r[b];
+    }
+    acc.r[2] += s2 * wr;
+    acc.i[2] += s2 * wi;
 }
 
-// acc -= U^dag v, (U^dag)_{ab} = conj(U_{ba})
+// acc -= U^dag v, (U^dag)_{ab} = conj(U_{ba}), row 2 of U scaled by s2
 template <typename T>
-__device__ __forceinline__ void adj_mul_sub(const Mat3<T> &u, const Vec3<T> &v, Vec3<T> &acc)
+__device__ __forceinline__ void adj_mul_sub(const Mat3<T> &u, const Vec3<T> &v, Vec3<T> &acc, T s2)
 {
+    const T v2r = s2 * v.r[2], v2i = s2 * v.i[2];
 #pragma unroll
-    for (int a = 0; a < 3; ++a)
+    for (int a = 0; a < 3; ++a) {
 #pragma unroll
-        for (int b = 0; b < 3; ++b) {
+        for (int b = 0; b < 2; ++b) {
             acc.r[a] -= u.r[b][a] * v.r[b] + u.i[b][a] * v.i[b];
             acc.i[a] -= u.r[b][a] * v.i[b] - u.i[b][a] * v.r[b];
         }
+        acc.r[a] -= u.r[2][a] * v2r + u.i[2][a] * v2i;
+        acc.i[a] -= u.r[2][a] * v2i - u.i[2][a] * v2r;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -402,6 +607,87 @@ __device__ __forceinline__ double block_sum(double v, double *sm)
         for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
     }
     return s;  // valid in thread 0
+}
+
+// Compensated FP32 ("float-float") sums for FP32 data.  On GB300 one warp-
+// wide FP64 instruction occupies the FP64 pipe for ~16 cycles, so the
+// per-thread, warp and block levels add (hi, lo) pairs with an exact two-sum
+// in FP32 (~2^-44 relative), the partials are float2, and only the final
+// total becomes a double.  FP64 data keeps the FP64 path above.
+struct FF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ FF ff_add(FF a, FF b)
+{
+    const float s = a.hi + b.hi;
+    const float bb = s - a.hi;
+    const float e = (a.hi - (s - bb)) + (b.hi - bb);
+    FF r;
+    r.hi = s;
+    r.lo = e + (a.lo + b.lo);
+    return r;
+}
+
+__device__ __forceinline__ FF ff_shfl_down(FF a, int o)
+{
+    FF b;
+    b.hi = __shfl_down_sync(0xffffffffu, a.hi, o);
+    b.lo = __shfl_down_sync(0xffffffffu, a.lo, o);
+    return b;
+}
+
+template <int BS>
+__device__ __forceinline__ FF block_sum_ff(FF v, float2 *sm)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = ff_add(v, ff_shfl_down(v, o));
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sm[w] = make_float2(v.hi, v.lo);
+    __syncthreads();
+    FF s = {0.f, 0.f};
+    if (w == 0) {
+        if (lane < BS / 32) {
+            s.hi = sm[lane].x;
+            s.lo = sm[lane].y;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s = ff_add(s, ff_shfl_down(s, o));
+    }
+    return s;  // valid in thread 0
+}
+
+template <int BS>
+__device__ __forceinline__ bool grid_sum_ff(FF v, float2 *partials, unsigned *counter, double &total)
+{
+    __shared__ float2 smf[32];
+    __shared__ int is_last_ff;
+    FF s = block_sum_ff<BS>(v, smf);
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = make_float2(s.hi, s.lo);
+        __threadfence();
+        unsigned ticket = atomicAdd(counter, 1u);
+        is_last_ff = (ticket == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!is_last_ff) return false;
+    __threadfence();
+    FF acc = {0.f, 0.f};
+    for (int k = threadIdx.x; k < (int)gridDim.x; k += BS) {
+        const float2 p = __ldcg(partials + k);
+        FF q;
+        q.hi = p.x;
+        q.lo = p.y;
+        acc = ff_add(acc, q);
+    }
+    FF t = block_sum_ff<BS>(acc, smf);
+    if (threadIdx.x == 0) {
+        total = (double)t.hi + (double)t.lo;
+        *counter = 0u;
+        return true;
+    }
+    return false;
 }
 
 // Returns true in thread 0 of the last block, with the grid total in `total`.

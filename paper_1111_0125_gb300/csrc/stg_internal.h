@@ -63,14 +63,16 @@ struct Workspace {
     size_t n_partials = 0;
     CGState *state = nullptr;      // device
     CGState *state_host = nullptr; // pinned mirror for read-back
-    void *tmp[3] = {nullptr, nullptr, nullptr};  // odd intermediate per precision
+    void *tmp[4] = {nullptr, nullptr, nullptr, nullptr};  // odd intermediate per precision
     // CG vectors (allocated by the solver)
     void *x64 = nullptr, *b64 = nullptr, *r64 = nullptr, *t64 = nullptr;
     void *y = nullptr, *r = nullptr, *d = nullptr, *q = nullptr;
     int cg_sloppy = -1;
-    cudaGraphExec_t graph = nullptr;
-    int graph_sloppy = -1, graph_iters = 0, graph_timing = 0;
-    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // timing events
+    // captured chunks of iterations: [0] plain, [1] with per-kernel events
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    int graph_sloppy[2] = {-1, -1}, graph_iters[2] = {0, 0};
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // per-kernel events
+    cudaEvent_t ev_chunk[2] = {nullptr, nullptr};                        // around plain chunks
 };
 
 stg_status workspace_get(stg_gauge *g, Workspace **out);
@@ -95,6 +97,26 @@ struct DslashLaunch {
 };
 
 stg_status launch_dslash(const Geom &g, int prec, int epi, const DslashLaunch &a, cudaStream_t s);
+
+// kernel arguments of every Dslash variant
+struct DslashArgs {
+    Geom g;
+    const char *lf[4];  // forward link blocks  (parity p,   mu)
+    const char *lb[4];  // backward link blocks (parity 1-p, mu)
+    int parity;
+    const void *in;
+    void *out;
+    const void *w;
+    const void *v;
+    double m2;
+    double *dot;
+    CGState *state;
+    double *partials;
+    unsigned *counter;
+};
+
+// FX16 Dslash, two sites per thread on packed FP32x2 arithmetic
+void launch_dslash_fx2(int recon, int epi, const DslashArgs &a, cudaStream_t s);
 
 int grid_for(long n);
 

@@ -5,6 +5,8 @@ Tolerances (norm-wise relative error of the whole output field):
                             order of the 8 x 9 complex multiply-adds)
   FP32            : 1e-6   (24-bit significand, ~10^2 rounding steps)
   FP16 storage    : 2e-3   (11-bit significand on links and fields)
+  FX16 storage    : 1e-4   (16-bit fixed point: |error| <= 2^-16 of the site's
+                            largest component, links to 2^-16 absolute)
 CG: the true residual |b - A x| / |b| computed with the *oracle's* A is <= tol,
 and |x - x_oracle| / |x_oracle| <= kappa_hat * tol, kappa_hat = (m^2+64)/m^2.
 """
@@ -19,7 +21,7 @@ from paper_1111_0125_gb300 import Gauge
 
 pytestmark = pytest.mark.gpu
 
-TOL = {stg.STG_FP64: 1e-12, stg.STG_FP32: 1e-6, stg.STG_FP16: 2e-3}
+TOL = {stg.STG_FP64: 1e-12, stg.STG_FP32: 1e-6, stg.STG_FP16: 2e-3, stg.STG_FX16: 1e-4}
 
 # several tiles and ragged tails: Vh = 128, 8, 192, 1440, 2520, 20736
 DIMS = [(4, 4, 4, 4), (2, 2, 2, 2), (4, 6, 2, 8), (6, 4, 10, 12), (10, 6, 6, 14),
@@ -46,7 +48,7 @@ def _cuda():
     torch.cuda.synchronize()
 
 
-@pytest.mark.parametrize("prec", [stg.STG_FP64, stg.STG_FP32, stg.STG_FP16])
+@pytest.mark.parametrize("prec", [stg.STG_FP64, stg.STG_FP32, stg.STG_FP16, stg.STG_FX16])
 def test_pack_unpack_roundtrip(prec):
     dims = (6, 4, 10, 12)
     U = _links(dims)
@@ -56,13 +58,14 @@ def test_pack_unpack_roundtrip(prec):
     if prec == stg.STG_FP64:
         assert np.array_equal(back, chi)
     else:
-        assert rel(back, chi) < {stg.STG_FP32: 1e-7, stg.STG_FP16: 1e-3}[prec]
+        assert rel(back, chi) < {stg.STG_FP32: 1e-7, stg.STG_FP16: 1e-3, stg.STG_FX16: 5e-5}[prec]
 
 
 @pytest.mark.parametrize("dims", DIMS)
 @pytest.mark.parametrize("prec,recon", [(stg.STG_FP64, 18), (stg.STG_FP64, 12),
                                         (stg.STG_FP32, 18), (stg.STG_FP32, 12),
-                                        (stg.STG_FP16, 18), (stg.STG_FP16, 12)])
+                                        (stg.STG_FP16, 18), (stg.STG_FP16, 12),
+                                        (stg.STG_FX16, 18), (stg.STG_FX16, 12)])
 def test_dslash_matches_oracle(dims, prec, recon):
     U = _links(dims, "haar", seed=sum(dims))
     with Gauge(dims, U, sloppy=prec, recon=recon) as g:
@@ -75,7 +78,8 @@ def test_dslash_matches_oracle(dims, prec, recon):
 
 @pytest.mark.parametrize("dims", [(4, 4, 4, 4), (6, 4, 10, 12), (12, 12, 12, 24)])
 @pytest.mark.parametrize("prec,recon", [(stg.STG_FP64, 18), (stg.STG_FP32, 18),
-                                        (stg.STG_FP32, 12), (stg.STG_FP16, 12)])
+                                        (stg.STG_FP32, 12), (stg.STG_FP16, 12),
+                                        (stg.STG_FX16, 12)])
 def test_apply_A_and_dot_match_oracle(dims, prec, recon):
     U = _links(dims, "exp", seed=3, eps=0.4)
     mass = 0.05
@@ -134,7 +138,8 @@ def test_cg_fp64_c1():
 
 
 @pytest.mark.parametrize("sloppy,recon", [(stg.STG_FP32, 18), (stg.STG_FP32, 12),
-                                          (stg.STG_FP16, 12), (stg.STG_FP16, 18)])
+                                          (stg.STG_FP16, 12), (stg.STG_FP16, 18),
+                                          (stg.STG_FX16, 12), (stg.STG_FX16, 18)])
 @pytest.mark.parametrize("policy", [stg.STG_CG_RELIABLE, stg.STG_CG_REFINE])
 def test_cg_mixed_matches_oracle(sloppy, recon, policy):
     dims, mass, tol = (8, 8, 8, 8), 0.05, 1e-10
