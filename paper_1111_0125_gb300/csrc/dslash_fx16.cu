@@ -18,6 +18,10 @@
 // phase), i.e. U_2b = (s / 32767) conj(c_b).
 #include "stg_internal.h"
 
+#ifndef STG_FX2_MINBLOCKS
+#define STG_FX2_MINBLOCKS 2
+#endif
+
 namespace stg {
 
 typedef float2 f2;
@@ -165,10 +169,22 @@ __device__ __forceinline__ void bwd2(const Mat3x2 &u, const Vec3x2 &v, f2 s2, Ac
     }
 }
 
-// the scalar epilogue of one site (same arithmetic as k_dslash's)
+// decode one FX16 site record already in registers
+__device__ __forceinline__ Vec3<float> fx_decode(uint4 u)
+{
+    const float sc = __uint_as_float(u.w);
+    Vec3<float> v;
+    v.r[0] = fx_lo(u.x) * sc; v.i[0] = fx_hi(u.x) * sc;
+    v.r[1] = fx_lo(u.y) * sc; v.i[1] = fx_hi(u.y) * sc;
+    v.r[2] = fx_lo(u.z) * sc; v.i[2] = fx_hi(u.z) * sc;
+    return v;
+}
+
+// the scalar epilogue of one site (same arithmetic as k_dslash's); wraw is
+// the site's record of w, loaded at kernel start for the A epilogues
 template <int EPI>
 __device__ __forceinline__ float epilogue(const DslashArgs &a, int vh, int i, const Vec3<float> &acc,
-                                          float m2)
+                                          float m2, uint4 wraw)
 {
     float dot = 0.f;
     if (EPI == EPI_NONE || EPI == EPI_GATE) {
@@ -186,7 +202,7 @@ __device__ __forceinline__ float epilogue(const DslashArgs &a, int vh, int i, co
 #pragma unroll
         for (int c = 0; c < 3; ++c) dot += os.r[c] * os.r[c] + os.i[c] * os.i[c];
     } else {
-        const Vec3<float> d = FieldIO<PX16>::load_nc(a.w, vh, i);
+        const Vec3<float> d = fx_decode(wraw);
         Vec3<float> o;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -201,7 +217,7 @@ __device__ __forceinline__ float epilogue(const DslashArgs &a, int vh, int i, co
 }
 
 template <int R, int EPI>
-__global__ void __launch_bounds__(kBlock, 2) k_dslash_fx2(const DslashArgs a)
+__global__ void __launch_bounds__(kBlock, STG_FX2_MINBLOCKS) k_dslash_fx2(const DslashArgs a)
 {
     if (EPI == EPI_A_CG || EPI == EPI_GATE) {
         if (a.state->flag != FLAG_RUN) return;  // uniform over the grid
@@ -213,6 +229,13 @@ __global__ void __launch_bounds__(kBlock, 2) k_dslash_fx2(const DslashArgs a)
     FF dot = {0.f, 0.f};
     if (okA) {
         const int jA = iA, jB = okB ? iB : iA;  // a missing B recomputes A, unstored
+        // the A epilogues read w = d at the output sites: issue those loads
+        // first so their latency hides under the half-pass
+        uint4 wA = make_uint4(0u, 0u, 0u, 0u), wB = wA;
+        if (EPI == EPI_A || EPI == EPI_A_DOT || EPI == EPI_A_CG) {
+            wA = __ldg(static_cast<const uint4 *>(a.w) + jA);
+            wB = __ldg(static_cast<const uint4 *>(a.w) + jB);
+        }
         const Site sA = site_of(a.g, jA, a.parity);
         const Site sB = site_of(a.g, jB, a.parity);
         Acc2 A;
@@ -253,9 +276,9 @@ __global__ void __launch_bounds__(kBlock, 2) k_dslash_fx2(const DslashArgs a)
             accB.i[c] = im.y;
         }
         const float m2 = (EPI == EPI_A_CG) ? float(a.state->m2) : float(a.m2);
-        const float dA = epilogue<EPI>(a, vh, iA, accA, m2);
+        const float dA = epilogue<EPI>(a, vh, iA, accA, m2, wA);
         float dB = 0.f;
-        if (okB) dB = epilogue<EPI>(a, vh, iB, accB, m2);
+        if (okB) dB = epilogue<EPI>(a, vh, iB, accB, m2, wB);
         dot.hi = dA;
         dot = ff_add(dot, FF{dB, 0.f});
     }
