@@ -32,6 +32,7 @@ __all__ = [
     "source",
     "gauge_transform",
     "lattice_volume",
+    "log_uniform",
 ]
 
 
@@ -143,3 +144,9 @@ def gauge_transform(dims, seed: int = 7) -> np.ndarray:
     """Haar SU(3) matrix per site, [Lt][Lz][Ly][Lx][3][3]."""
     lx, ly, lz, lt = (int(d) for d in dims)
     return haar_su3(rng(seed), lattice_volume(dims)).reshape(lt, lz, ly, lx, 3, 3)
+
+
+def log_uniform(n: int, lo: float, hi: float, seed: int) -> np.ndarray:
+    """n values log-uniform in [lo, hi] (e.g. quark masses of a batch)."""
+    g = rng(seed)
+    return np.exp(g.uniform(np.log(lo), np.log(hi), size=int(n)))

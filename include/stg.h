@@ -234,6 +234,47 @@ stg_status stg_apply_A_dot_noalloc(const stg_gauge *g, double mass, const void *
                                    void *out_dev, double *dot_dev, stg_prec prec,
                                    stg_stream_t stream);
 
+/*
+ * Several right-hand sides on one gauge field (the batched path).  A batch is
+ * `nrhs` (1..64) consecutive fields, each in the device layout of `prec`
+ * (stg_field_bytes apart).  The multi-system kernels load every link once
+ * per register block of NB systems, so the link traffic per system falls by
+ * NB; NB (1, 2, 4, 8) and the thread-block size (128, 256) come from an
+ * autotuner that times the candidates on the first call for a (lattice,
+ * precision, reconstruction, nrhs) and caches the choice for the process
+ * (and, when the environment variable STG_TUNE_CACHE names a file, in that
+ * file).  prec must be FP32 or FX16 and held by the handle.
+ *
+ * stg_dslash_mrhs: out_k = D_{p <- 1-p} in_k for k < nrhs (Eq. 5).
+ */
+stg_status stg_dslash_mrhs(const stg_gauge *g, int out_parity, int nrhs, const void *in_dev,
+                           void *out_dev, stg_prec prec, stg_stream_t stream);
+
+/* out_k = m_k^2 in_k - D_eo D_oe in_k (Eq. 3) with masses[k] (host array). */
+stg_status stg_apply_A_mrhs(const stg_gauge *g, int nrhs, const double *masses, const void *in_dev,
+                            void *out_dev, stg_prec prec, stg_stream_t stream);
+
+/*
+ * Solve A_k x_k = b_k for k < nrhs with the mixed-precision CG of Sec. 3.2
+ * (policy RELIABLE or REFINE; inner precision params->sloppy, FP32 or FX16),
+ * batched: every inner iteration advances all unconverged systems with the
+ * multi-system kernels, each system keeping its own alpha, beta, residual,
+ * updates and convergence test (a converged system drops out of the batch).
+ *   src_dev / x_dev: nrhs consecutive canonical complex128 [Vh][3] fields
+ *   (x_dev holds the initial guesses on entry); masses: host array;
+ *   stats: NULL or nrhs entries.
+ * Returns STG_OK when every system converged, else the first error;
+ * STG_ERR_NOT_CONVERGED if any system reached maxiter (all x_k written).
+ */
+stg_status stg_cg_solve_mrhs(const stg_gauge *g, int nrhs, const double *src_dev, double *x_dev,
+                             const double *masses, double tol, const stg_cg_params *params,
+                             stg_cg_stats *stats, stg_stream_t stream);
+
+/* The autotuner's choice (rhs_block = NB, threads per block) for this
+ * handle's lattice, `prec` and nrhs; STG_ERR_INVALID_ARG if not tuned yet. */
+stg_status stg_mrhs_tuning(const stg_gauge *g, stg_prec prec, int nrhs, int *rhs_block,
+                           int *threads);
+
 /* Fill params with the defaults: RELIABLE, sloppy = handle's sloppy
  * precision, delta = 0.1, maxiter = 0 (10 N_dim), check_every = 0 (auto),
  * timing = 0. */

@@ -86,6 +86,10 @@ def _load():
         "stg_apply_A_dot_noalloc": (i, [p, d, p, p, p, i, p]),
         "stg_cg_params_default": (i, [p, p]),
         "stg_cg_solve": (i, [p, p, p, d, d, p, p, p]),
+        "stg_dslash_mrhs": (i, [p, i, i, p, p, i, p]),
+        "stg_apply_A_mrhs": (i, [p, i, p, p, p, i, p]),
+        "stg_cg_solve_mrhs": (i, [p, i, p, p, p, d, p, p, p]),
+        "stg_mrhs_tuning": (i, [p, i, i, p, p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -219,6 +223,45 @@ def stg_cg_solve(handle: int, src_dev, x_dev, mass: float, tol: float, params=No
                           ctypes.byref(stats), _stream(stream))
     _check(st, "stg_cg_solve", stats.as_dict())
     return stats.as_dict()
+
+
+def stg_dslash_mrhs(handle: int, out_parity: int, nrhs: int, in_dev, out_dev, prec: int,
+                    stream=None) -> None:
+    """out_k = D in_k for nrhs consecutive fields of one precision."""
+    _check(lib.stg_dslash_mrhs(handle, int(out_parity), int(nrhs), _ptr(in_dev), _ptr(out_dev),
+                               int(prec), _stream(stream)), "stg_dslash_mrhs")
+
+
+def stg_apply_A_mrhs(handle: int, nrhs: int, masses, in_dev, out_dev, prec: int,
+                     stream=None) -> None:
+    m = np.ascontiguousarray(np.asarray(masses, dtype=np.float64).reshape(-1))
+    if m.size != nrhs:
+        raise StgError(STG_ERR_INVALID_ARG, "stg_apply_A_mrhs", "need one mass per system")
+    _check(lib.stg_apply_A_mrhs(handle, int(nrhs), m.ctypes.data, _ptr(in_dev), _ptr(out_dev),
+                                int(prec), _stream(stream)), "stg_apply_A_mrhs")
+
+
+def stg_cg_solve_mrhs(handle: int, nrhs: int, src_dev, x_dev, masses, tol: float, params=None,
+                      stream=None) -> list:
+    """Batched solve of nrhs systems; returns one stats dict per system and
+    raises StgError (with .stats = that list) on any non-OK status."""
+    m = np.ascontiguousarray(np.asarray(masses, dtype=np.float64).reshape(-1))
+    if m.size != nrhs:
+        raise StgError(STG_ERR_INVALID_ARG, "stg_cg_solve_mrhs", "need one mass per system")
+    stats = (stg_cg_stats * nrhs)()
+    pp = ctypes.byref(params) if params is not None else None
+    st = lib.stg_cg_solve_mrhs(handle, int(nrhs), _ptr(src_dev), _ptr(x_dev), m.ctypes.data,
+                               float(tol), pp, stats, _stream(stream))
+    out = [s.as_dict() for s in stats]
+    _check(st, "stg_cg_solve_mrhs", out)
+    return out
+
+
+def stg_mrhs_tuning(handle: int, prec: int, nrhs: int):
+    nb, bs = ctypes.c_int(), ctypes.c_int()
+    _check(lib.stg_mrhs_tuning(handle, int(prec), int(nrhs), ctypes.byref(nb), ctypes.byref(bs)),
+           "stg_mrhs_tuning")
+    return nb.value, bs.value
 
 
 from .fields import Gauge  # noqa: E402  (convenience layer over the names above)

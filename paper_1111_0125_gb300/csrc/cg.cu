@@ -67,8 +67,8 @@ static int grid_vec(long n, int pr)
 // vector kernels (grid-stride, FP64 reductions)
 // ---------------------------------------------------------------------------
 template <int PD, int PR>
-__global__ void __launch_bounds__(kBlock, kVecBlocksPerSM)
-k_cg_update(int vh, void *y, void *r, const void *d, const void *q, CGState *st, double *partials)
+__device__ __forceinline__ void cg_update_body(int vh, void *y, void *r, const void *d, const void *q,
+                                               CGState *st, double *partials)
 {
     if (st->flag != FLAG_RUN) return;
     typedef typename Real<PR>::T T;
@@ -138,7 +138,26 @@ k_cg_update(int vh, void *y, void *r, const void *d, const void *q, CGState *st,
 
 template <int PD, int PR>
 __global__ void __launch_bounds__(kBlock, kVecBlocksPerSM)
-k_xpay(int vh, const void *r, void *d, const CGState *st)
+k_cg_update(int vh, void *y, void *r, const void *d, const void *q, CGState *st, double *partials)
+{
+    cg_update_body<PD, PR>(vh, y, r, d, q, st, partials);
+}
+
+// several systems: blockIdx.y is the slot in the active list
+template <int PD, int PR>
+__global__ void __launch_bounds__(kBlock, kVecBlocksPerSM)
+k_cg_update_m(int vh, char *y, char *r, const char *d, const char *q, size_t sr, size_t sd,
+              CGState *states, double *partials, size_t pstride, const int *active,
+              const int *nactive)
+{
+    if ((int)blockIdx.y >= *nactive) return;
+    const int k = active[blockIdx.y];
+    cg_update_body<PD, PR>(vh, y + k * sr, r + k * sr, d + k * sd, q + k * sd, states + k,
+                           partials + k * pstride);
+}
+
+template <int PD, int PR>
+__device__ __forceinline__ void xpay_body(int vh, const void *r, void *d, const CGState *st)
 {
     if (st->flag != FLAG_RUN) return;
     typedef typename Real<PR>::T T;
@@ -171,6 +190,23 @@ k_xpay(int vh, const void *r, void *d, const CGState *st)
             }
         }
     }
+}
+
+template <int PD, int PR>
+__global__ void __launch_bounds__(kBlock, kVecBlocksPerSM)
+k_xpay(int vh, const void *r, void *d, const CGState *st)
+{
+    xpay_body<PD, PR>(vh, r, d, st);
+}
+
+template <int PD, int PR>
+__global__ void __launch_bounds__(kBlock, kVecBlocksPerSM)
+k_xpay_m(int vh, const char *r, char *d, size_t sr, size_t sd, const CGState *states,
+         const int *active, const int *nactive)
+{
+    if ((int)blockIdx.y >= *nactive) return;
+    const int k = active[blockIdx.y];
+    xpay_body<PD, PR>(vh, r + k * sr, d + k * sd, states + k);
 }
 
 // x64 += y  (reliable update, Sec. 3.2: x_{k+1} = x_k + y_n in FP64)
@@ -322,6 +358,92 @@ static stg_status cuda_check_launch()
 {
     STG_CUDA(cudaGetLastError());
     return STG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// launch helpers with explicit operands (used by the multi-system solver)
+// ---------------------------------------------------------------------------
+int vec_grid(long n, int pd) { return grid_vec(n, pr_of(pd)); }
+
+stg_status launch_update_m(int pd, int vh, char *y, char *r, const char *d, const char *q, size_t sr,
+                           size_t sd, CGState *states, double *partials, size_t pstride,
+                           const int *active, const int *nactive, int nslots, cudaStream_t s)
+{
+    const dim3 grid(grid_vec(vh, pr_of(pd)), nslots);
+    if (pd == P64)
+        k_cg_update_m<P64, P64><<<grid, kBlock, 0, s>>>(vh, y, r, d, q, sr, sd, states, partials, pstride, active, nactive);
+    else if (pd == P32)
+        k_cg_update_m<P32, P32><<<grid, kBlock, 0, s>>>(vh, y, r, d, q, sr, sd, states, partials, pstride, active, nactive);
+    else if (pd == P16)
+        k_cg_update_m<P16, P32><<<grid, kBlock, 0, s>>>(vh, y, r, d, q, sr, sd, states, partials, pstride, active, nactive);
+    else
+        k_cg_update_m<PX16, P32><<<grid, kBlock, 0, s>>>(vh, y, r, d, q, sr, sd, states, partials, pstride, active, nactive);
+    STG_CUDA(cudaGetLastError());
+    return STG_OK;
+}
+
+stg_status launch_xpay_m(int pd, int vh, const char *r, char *d, size_t sr, size_t sd,
+                         const CGState *states, const int *active, const int *nactive, int nslots,
+                         cudaStream_t s)
+{
+    const dim3 grid(grid_vec(vh, pr_of(pd)), nslots);
+    if (pd == P64) k_xpay_m<P64, P64><<<grid, kBlock, 0, s>>>(vh, r, d, sr, sd, states, active, nactive);
+    else if (pd == P32) k_xpay_m<P32, P32><<<grid, kBlock, 0, s>>>(vh, r, d, sr, sd, states, active, nactive);
+    else if (pd == P16) k_xpay_m<P16, P32><<<grid, kBlock, 0, s>>>(vh, r, d, sr, sd, states, active, nactive);
+    else k_xpay_m<PX16, P32><<<grid, kBlock, 0, s>>>(vh, r, d, sr, sd, states, active, nactive);
+    STG_CUDA(cudaGetLastError());
+    return STG_OK;
+}
+
+stg_status launch_reset(int pd, int vh, void *y, void *r, void *d, const void *r64, double beta,
+                        int copy_r, cudaStream_t s)
+{
+    const int grid = grid_for(vh);
+    STG_DISPATCH_PD(pd, k_reset, vh, y, r, d, r64, beta, copy_r);
+    STG_CUDA(cudaGetLastError());
+    return STG_OK;
+}
+
+stg_status launch_accumulate_x(int pr, int vh, void *x64, const void *y, cudaStream_t s)
+{
+    const int grid = grid_for(vh);
+    if (pr == P64) k_accumulate_x<P64><<<grid, kBlock, 0, s>>>(vh, x64, y);
+    else k_accumulate_x<P32><<<grid, kBlock, 0, s>>>(vh, x64, y);
+    STG_CUDA(cudaGetLastError());
+    return STG_OK;
+}
+
+stg_status launch_norm2(int prec, int vh, const void *v, CGState *st, double *partials, cudaStream_t s)
+{
+    const int grid = grid_for(vh);
+    if (prec == P64) k_norm2<P64><<<grid, kBlock, 0, s>>>(vh, v, st, partials);
+    else if (prec == P32) k_norm2<P32><<<grid, kBlock, 0, s>>>(vh, v, st, partials);
+    else if (prec == P16) k_norm2<P16><<<grid, kBlock, 0, s>>>(vh, v, st, partials);
+    else k_norm2<PX16><<<grid, kBlock, 0, s>>>(vh, v, st, partials);
+    STG_CUDA(cudaGetLastError());
+    return STG_OK;
+}
+
+// r64 = b64 - A x64 with the FP64 operator, |r64|^2 -> st->result (no sync)
+stg_status launch_true_residual(stg_gauge *g, const void *x64, const void *b64, void *r64, void *t64,
+                                double m2, CGState *st, double *partials, cudaStream_t s)
+{
+    DslashLaunch L = {};
+    L.links = &g->hi;
+    L.out_parity = 1;
+    L.in = x64;
+    L.out = t64;
+    STG_TRY(launch_dslash(g->geom, P64, EPI_NONE, L, s));
+    L.out_parity = 0;
+    L.in = t64;
+    L.out = r64;
+    L.w = b64;
+    L.v = x64;
+    L.m2 = m2;
+    L.dot = &st->result;
+    L.partials = partials;
+    L.counter = &st->counter;
+    return launch_dslash(g->geom, P64, EPI_RES, L, s);
 }
 
 static stg_status alloc_vec(void **p, size_t bytes)

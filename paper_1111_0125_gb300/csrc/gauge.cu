@@ -317,6 +317,8 @@ stg_status workspace_tmp(stg_gauge *g, int prec, void **out)
 void workspace_free(Workspace *ws)
 {
     if (!ws) return;
+    mrhs_free(ws->mrhs);
+    cudaFree(ws->mrhs_tmp);
     for (int k = 0; k < 2; ++k)
         if (ws->graph[k]) cudaGraphExecDestroy(ws->graph[k]);
     for (int k = 0; k < 5; ++k)

@@ -1,0 +1,232 @@
+// Multi-right-hand-side Dslash (Eq. 5) and its fused A epilogue (Eq. 3).
+//
+// One gauge field, N colour-vector fields (N consecutive device fields of
+// one precision).  Each thread owns one output site and walks the right-hand
+// sides in register blocks of NB: the site's eight links are loaded (and
+// decoded / rebuilt) once per block and applied to NB input fields, so the
+// link bytes per site and right-hand side fall from 8L to 8L / NB while the
+// field bytes stay 2S (3S with the fused epilogue).  NB and the block size BS
+// are template parameters picked by the autotuner in mrhs.cu.
+//
+// The right-hand sides processed are those of a device-side list (active,
+// nactive) so that the host can drop converged systems between chunks
+// without recapturing the CUDA graph; inside a chunk the per-system CG flag
+// is checked as well.  The fused epilogue reduces d_k^dag q_k per system in
+// compensated FP32 pairs (block partials per system, last block finishes all
+// systems in a fixed order).
+#pragma once
+
+#include "stg_internal.h"
+
+namespace stg {
+
+constexpr int kMaxRhs = 64;
+
+struct MrhsArgs {
+    Geom g;
+    const char *lf[4];
+    const char *lb[4];
+    int parity;
+    const char *in;
+    char *out;
+    const char *w;         // EPI_A / EPI_A_CG: the even inputs d
+    size_t fstride;        // bytes between consecutive right-hand-side fields
+    int nrhs;              // number of systems (slots)
+    const int *active;     // device list of systems to process; NULL: all
+    const int *nactive;    // device count for `active`
+    CGState *states;       // per system (EPI_GATE, EPI_A_CG)
+    float m2[kMaxRhs];     // EPI_A: m_k^2
+    float2 *partials;      // EPI_A_CG: [nrhs][gridDim.x]
+    unsigned *counter;     // EPI_A_CG: arrival counter
+};
+
+template <int P, int R, int NB, int EPI, int BS>
+__global__ void __launch_bounds__(BS) k_dslash_m(const MrhsArgs a)
+{
+    typedef typename Real<P>::T T;
+    const int vh = a.g.Vh;
+    const int i = blockIdx.x * BS + threadIdx.x;
+    const bool ok = i < vh;
+    const int nact = a.active ? *a.nactive : a.nrhs;
+
+    int jf[4] = {0, 0, 0, 0}, jb[4] = {0, 0, 0, 0};
+    T s2f[4], s2b[4];
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) s2f[mu] = s2b[mu] = T(1);
+    if (ok) {
+        const Site s = site_of(a.g, i, a.parity);
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) {
+            neighbours(a.g, s, i, mu, jf[mu], jb[mu]);
+            if (R == 12) {
+                float sf, sb;
+                link_signs(a.g, s, mu, sf, sb);
+                s2f[mu] = T(sf * LinkPost<P>::row2);
+                s2b[mu] = T(sb * LinkPost<P>::row2);
+            }
+        }
+    }
+
+    __shared__ float2 red[NB][BS / 32];
+    for (int k0 = 0; k0 < nact; k0 += NB) {
+        int rid[NB];
+        bool run[NB];
+#pragma unroll
+        for (int q = 0; q < NB; ++q) {
+            const int kk = k0 + q;
+            run[q] = kk < nact;
+            rid[q] = run[q] ? (a.active ? a.active[kk] : kk) : 0;
+            if (EPI == EPI_GATE || EPI == EPI_A_CG)
+                run[q] = run[q] && a.states[rid[q]].flag == FLAG_RUN;
+        }
+        Vec3<T> acc[NB];
+#pragma unroll
+        for (int q = 0; q < NB; ++q)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) acc[q].r[c] = acc[q].i[c] = T(0);
+        FF dot[NB];
+#pragma unroll
+        for (int q = 0; q < NB; ++q) dot[q].hi = dot[q].lo = 0.f;
+        if (ok) {
+#pragma unroll
+            for (int mu = 0; mu < 4; ++mu) {
+                const Mat3<T> uf = LinkIO<P, R>::load(a.lf[mu], vh, i);
+#pragma unroll
+                for (int q = 0; q < NB; ++q)
+                    if (run[q]) {
+                        const Vec3<T> v = FieldIO<P>::load_nc(a.in + rid[q] * a.fstride, vh, jf[mu]);
+                        mul_add(uf, v, acc[q], s2f[mu]);
+                    }
+                const Mat3<T> ub = LinkIO<P, R>::load(a.lb[mu], vh, jb[mu]);
+#pragma unroll
+                for (int q = 0; q < NB; ++q)
+                    if (run[q]) {
+                        const Vec3<T> v = FieldIO<P>::load_nc(a.in + rid[q] * a.fstride, vh, jb[mu]);
+                        adj_mul_sub(ub, v, acc[q], s2b[mu]);
+                    }
+            }
+#pragma unroll
+            for (int q = 0; q < NB; ++q) {
+                if (!run[q]) continue;
+                if (P == PX16) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        acc[q].r[c] *= T(LinkPost<PX16>::k);
+                        acc[q].i[c] *= T(LinkPost<PX16>::k);
+                    }
+                }
+                char *out = a.out + rid[q] * a.fstride;
+                if (EPI == EPI_NONE || EPI == EPI_GATE) {
+                    FieldIO<P>::store(out, vh, i, acc[q]);
+                } else {
+                    const T m2 = (EPI == EPI_A_CG) ? T(a.states[rid[q]].m2) : T(a.m2[rid[q]]);
+                    const Vec3<T> d = FieldIO<P>::load_nc(a.w + rid[q] * a.fstride, vh, i);
+                    Vec3<T> o;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        o.r[c] = m2 * d.r[c] - acc[q].r[c];
+                        o.i[c] = m2 * d.i[c] - acc[q].i[c];
+                    }
+                    const Vec3<T> os = FieldIO<P>::store(out, vh, i, o);
+                    T dq = T(0);
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) dq += d.r[c] * os.r[c] + d.i[c] * os.i[c];
+                    dot[q].hi = float(dq);
+                }
+            }
+        }
+        if (EPI == EPI_A_CG) {
+            // per-system block partials: warp sums, then one pass over warps
+            const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+            for (int q = 0; q < NB; ++q) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) dot[q] = ff_add(dot[q], ff_shfl_down(dot[q], o));
+                if (lane == 0) red[q][w] = make_float2(dot[q].hi, dot[q].lo);
+            }
+            __syncthreads();
+            if ((int)threadIdx.x < NB && k0 + (int)threadIdx.x < nact) {
+                // system of slot threadIdx.x, recomputed (no dynamic register indexing)
+                const int kk = k0 + threadIdx.x;
+                const int k = a.active ? a.active[kk] : kk;
+                if (a.states[k].flag == FLAG_RUN) {
+                    FF s = {0.f, 0.f};
+#pragma unroll
+                    for (int ww = 0; ww < BS / 32; ++ww) {
+                        FF t;
+                        t.hi = red[threadIdx.x][ww].x;
+                        t.lo = red[threadIdx.x][ww].y;
+                        s = ff_add(s, t);
+                    }
+                    a.partials[(size_t)k * gridDim.x + blockIdx.x] = make_float2(s.hi, s.lo);
+                    __threadfence();
+                }
+            }
+            __syncthreads();
+        }
+    }
+
+    if (EPI == EPI_A_CG) {
+        __shared__ int is_last;
+        __shared__ float2 sm[32];
+        if (threadIdx.x == 0) {
+            __threadfence();
+            const unsigned ticket = atomicAdd(a.counter, 1u);
+            is_last = (ticket == gridDim.x - 1);
+        }
+        __syncthreads();
+        if (!is_last) return;
+        __threadfence();
+        for (int kk = 0; kk < nact; ++kk) {
+            const int k = a.active ? a.active[kk] : kk;
+            if (a.states[k].flag != FLAG_RUN) continue;  // uniform in the block
+            FF acc = {0.f, 0.f};
+            for (int b = threadIdx.x; b < (int)gridDim.x; b += BS) {
+                const float2 p = __ldcg(a.partials + (size_t)k * gridDim.x + b);
+                FF t;
+                t.hi = p.x;
+                t.lo = p.y;
+                acc = ff_add(acc, t);
+            }
+            const FF tot = block_sum_ff<BS>(acc, sm);
+            if (threadIdx.x == 0) {
+                CGState *st = a.states + k;
+                const double total = (double)tot.hi + (double)tot.lo;
+                st->pAp = total;
+                if (!(total > 0.0) || !isfinite(total)) st->flag = FLAG_BREAKDOWN;
+                else st->alpha = st->delta_new / total;
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) *a.counter = 0u;
+    }
+}
+
+// Launch one (P, R) family: picks the NB / BS instantiation at run time.
+template <int P, int R>
+void launch_m_pr(int nb, int bs, int epi, const MrhsArgs &a, cudaStream_t s)
+{
+#define STG_M_EPI(NB_, BS_)                                                                      \
+    do {                                                                                         \
+        const int grid = (a.g.Vh + BS_ - 1) / BS_;                                               \
+        switch (epi) {                                                                           \
+        case EPI_NONE: k_dslash_m<P, R, NB_, EPI_NONE, BS_><<<grid, BS_, 0, s>>>(a); break;      \
+        case EPI_A: k_dslash_m<P, R, NB_, EPI_A, BS_><<<grid, BS_, 0, s>>>(a); break;            \
+        case EPI_GATE: k_dslash_m<P, R, NB_, EPI_GATE, BS_><<<grid, BS_, 0, s>>>(a); break;      \
+        case EPI_A_CG: k_dslash_m<P, R, NB_, EPI_A_CG, BS_><<<grid, BS_, 0, s>>>(a); break;      \
+        }                                                                                        \
+    } while (0)
+#define STG_M_NB(BS_)                                  \
+    do {                                               \
+        if (nb == 1) STG_M_EPI(1, BS_);                \
+        else if (nb == 2) STG_M_EPI(2, BS_);           \
+        else if (nb == 4) STG_M_EPI(4, BS_);           \
+        else STG_M_EPI(8, BS_);                        \
+    } while (0)
+    if (bs == 128) STG_M_NB(128);
+    else STG_M_NB(256);
+#undef STG_M_NB
+#undef STG_M_EPI
+}
+
+}  // namespace stg

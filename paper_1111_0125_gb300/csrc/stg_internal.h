@@ -23,6 +23,24 @@ struct LinkField {
 
 struct Workspace;
 
+// Workspace of the multi-system CG (mrhs.cu): n systems of every vector.
+struct MrhsWs {
+    int nrhs = 0, pd = -1;
+    size_t f64 = 0, fr = 0, fd = 0;   // bytes of one FP64 / PR / PD field
+    size_t pstride = 0;               // reduction partials per system (doubles)
+    char *x64 = nullptr, *b64 = nullptr, *r64 = nullptr;
+    char *y = nullptr, *r = nullptr, *d = nullptr, *q = nullptr, *t = nullptr;
+    double *partials = nullptr;
+    CGState *states = nullptr, *states_host = nullptr;
+    int *active = nullptr, *active_host = nullptr;  // [0] = count, [1..] = systems
+    unsigned *counter = nullptr;
+    void *tmp = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    int graph_iters = 0;
+    int nb = 1, bs = 256, tuned_nb = -1;
+};
+void mrhs_free(MrhsWs *m);
+
 }  // namespace stg
 
 struct stg_gauge {
@@ -73,6 +91,9 @@ struct Workspace {
     int graph_sloppy[2] = {-1, -1}, graph_iters[2] = {0, 0};
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // per-kernel events
     cudaEvent_t ev_chunk[2] = {nullptr, nullptr};                        // around plain chunks
+    MrhsWs *mrhs = nullptr;           // multi-system solver
+    void *mrhs_tmp = nullptr;         // odd intermediates of stg_apply_A_mrhs
+    size_t mrhs_tmp_bytes = 0;
 };
 
 stg_status workspace_get(stg_gauge *g, Workspace **out);
@@ -119,5 +140,22 @@ struct DslashArgs {
 void launch_dslash_fx2(int recon, int epi, const DslashArgs &a, cudaStream_t s);
 
 int grid_for(long n);
+
+// vector-kernel helpers with explicit operands (cg.cu)
+int vec_grid(long n, int pd);
+stg_status launch_update_m(int pd, int vh, char *y, char *r, const char *d, const char *q, size_t sr,
+                           size_t sd, CGState *states, double *partials, size_t pstride,
+                           const int *active, const int *nactive, int nslots, cudaStream_t s);
+stg_status launch_xpay_m(int pd, int vh, const char *r, char *d, size_t sr, size_t sd,
+                         const CGState *states, const int *active, const int *nactive, int nslots,
+                         cudaStream_t s);
+stg_status launch_reset(int pd, int vh, void *y, void *r, void *d, const void *r64, double beta,
+                        int copy_r, cudaStream_t s);
+stg_status launch_accumulate_x(int pr, int vh, void *x64, const void *y, cudaStream_t s);
+stg_status launch_norm2(int prec, int vh, const void *v, CGState *st, double *partials, cudaStream_t s);
+stg_status launch_true_residual(stg_gauge *g, const void *x64, const void *b64, void *r64, void *t64,
+                                double m2, CGState *st, double *partials, cudaStream_t s);
+stg_status pack_field(const Geom &g, int prec, const double *canon, void *out, cudaStream_t s);
+stg_status unpack_field(const Geom &g, int prec, const void *in, double *canon, cudaStream_t s);
 
 }  // namespace stg
