@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--kernels-only", action="store_true")
+    ap.add_argument("--workload", default="c3", choices=["c3", "c4"],
+                    help="c3: 32^3x64 single solve (default); c4: 24^3x48, 16 systems batched")
+    ap.add_argument("--nrhs", type=int, default=16)
     ap.add_argument("--reps", type=int, default=3)
     return ap.parse_args()
 
@@ -244,6 +247,101 @@ def config_dict(args, dims):
 
 
 # ---------------------------------------------------------------------------
+# c4: one gauge field, 16 systems with masses log-uniform in [0.005, 0.05]
+# ---------------------------------------------------------------------------
+def run_c4(args):
+    import numpy as np
+    import torch
+
+    import gen
+    import paper_1111_0125_gb300 as stg
+    dims = (24, 24, 24, 48)
+    n = args.nrhs
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    U = gen.gauge_field(dims, "exp", seed=0, eps=0.5)
+    masses = gen.log_uniform(n, 0.005, 0.05, seed=17)
+    bs = gen.source(dims, seed=1, nrhs=n)
+    vh = bs.shape[1]
+    sloppy = {"f32": stg.STG_FP32, "fx16": stg.STG_FX16, "f16": stg.STG_FP16}[args.sloppy]
+    g = stg.Gauge(dims, U, sloppy=sloppy, recon=args.recon)
+    stream = torch.cuda.current_stream()
+    src = torch.from_numpy(np.ascontiguousarray(bs)).to(dev)
+    p = g.params(policy=stg.STG_CG_RELIABLE, sloppy=sloppy, delta=args.delta)
+
+    def batched():
+        x = torch.zeros_like(src)
+        return stg.stg_cg_solve_mrhs(g.handle, n, src, x, masses, args.tol, p, stream)
+
+    def one_by_one():
+        out = []
+        for k in range(n):
+            x = torch.zeros_like(src[k])
+            out.append(stg.stg_cg_solve(g.handle, src[k], x, masses[k], args.tol, p, stream))
+        return out
+
+    for _ in range(args.warmup):
+        batched()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    clocks = ClockSampler("")
+    e0.record(stream)
+    for _ in range(args.steps):
+        st = batched()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    t_batch = e0.elapsed_time(e1) / 1000.0 / args.steps
+    one_by_one()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    single = one_by_one()
+    torch.cuda.synchronize()
+    t_single = time.perf_counter() - t0
+    # the multi-system Dslash alone, back to back on this stream
+    fb = stg.stg_field_bytes(g.handle, sloppy)
+    fin = torch.empty(n * fb, dtype=torch.uint8, device=dev)
+    for k in range(n):
+        stg.stg_pack_field(g.handle, sloppy, src[k], fin[k * fb:(k + 1) * fb])
+    fout = torch.empty_like(fin)
+    stg.stg_dslash_mrhs(g.handle, 1, n, fin, fout, sloppy, stream)
+    nb, tb = stg.stg_mrhs_tuning(g.handle, sloppy, n)
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    for _ in range(20):
+        stg.stg_dslash_mrhs(g.handle, 1, n, fin, fout, sloppy, stream)
+    s1.record(stream)
+    s1.synchronize()
+    t_m = s0.elapsed_time(s1) / 20
+    L, S = LINK_BYTES[(args.sloppy, args.recon)], FIELD_BYTES[args.sloppy]
+    nbytes = vh * (8 * L * -(-n // nb) + 2 * S * n)
+    peak, src_ = measured_hbm()
+    achieved = nbytes / (t_m / 1000.0) / 1e9
+    print(json.dumps({
+        "metric": METRIC, "workload": "c4: 24^3x48, 16 systems batched, masses log-uniform "
+                                      "[0.005, 0.05], tol 1e-10",
+        "value": n / t_batch, "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000.0 * t_batch, "higher_is_better": True,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"lattice": "24x24x24x48", "nrhs": n, "sloppy_storage": args.sloppy,
+                   "recon": args.recon, "masses": [round(float(m), 6) for m in masses],
+                   "links": "exp(i*0.5*H), seed 0", "sources": "seed 1, drawn in sequence"},
+        "batched_seconds": t_batch, "one_by_one_seconds": t_single,
+        "speedup_batched_vs_one_by_one": t_single / t_batch,
+        "iters": [s_["iters"] for s_ in st], "updates": [s_["updates"] for s_ in st],
+        "true_res_max": max(s_["true_res"] for s_ in st),
+        "iters_one_by_one": [s_["iters"] for s_ in single],
+        "mrhs_dslash": {"rhs_block": nb, "threads": tb, "launch_ms": t_m,
+                        "algorithmic_bytes_per_launch": nbytes,
+                        "bytes_per_site_per_system": nbytes / vh / n,
+                        "achieved": achieved, "peak": peak, "peak_source": src_, "unit": "GB/s",
+                        "frac": achieved / peak,
+                        "gflops_576": vh * n * 576 / (t_m / 1000.0) / 1e9},
+        "clocks": ck,
+    }), flush=True)
+
+
+# ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
 def main():
@@ -251,6 +349,9 @@ def main():
     dims = tuple(int(v) for v in args.lattice.split(","))
     if args.impl == "reference":
         run_reference(args, dims)
+        return
+    if args.workload == "c4":
+        run_c4(args)
         return
     import numpy as np
     import torch

@@ -168,7 +168,6 @@ __global__ void __launch_bounds__(BS) k_dslash_m(const MrhsArgs a)
 
     if (EPI == EPI_A_CG) {
         __shared__ int is_last;
-        __shared__ float2 sm[32];
         if (threadIdx.x == 0) {
             __threadfence();
             const unsigned ticket = atomicAdd(a.counter, 1u);
@@ -177,27 +176,30 @@ __global__ void __launch_bounds__(BS) k_dslash_m(const MrhsArgs a)
         __syncthreads();
         if (!is_last) return;
         __threadfence();
-        for (int kk = 0; kk < nact; ++kk) {
+        // one warp per system (fixed summation order per system)
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+        for (int kk = w; kk < nact; kk += BS / 32) {
             const int k = a.active ? a.active[kk] : kk;
-            if (a.states[k].flag != FLAG_RUN) continue;  // uniform in the block
+            if (a.states[k].flag != FLAG_RUN) continue;  // uniform in the warp
             FF acc = {0.f, 0.f};
-            for (int b = threadIdx.x; b < (int)gridDim.x; b += BS) {
+            for (int b = lane; b < (int)gridDim.x; b += 32) {
                 const float2 p = __ldcg(a.partials + (size_t)k * gridDim.x + b);
                 FF t;
                 t.hi = p.x;
                 t.lo = p.y;
                 acc = ff_add(acc, t);
             }
-            const FF tot = block_sum_ff<BS>(acc, sm);
-            if (threadIdx.x == 0) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc = ff_add(acc, ff_shfl_down(acc, o));
+            if (lane == 0) {
                 CGState *st = a.states + k;
-                const double total = (double)tot.hi + (double)tot.lo;
+                const double total = (double)acc.hi + (double)acc.lo;
                 st->pAp = total;
                 if (!(total > 0.0) || !isfinite(total)) st->flag = FLAG_BREAKDOWN;
                 else st->alpha = st->delta_new / total;
             }
-            __syncthreads();
         }
+        __syncthreads();
         if (threadIdx.x == 0) *a.counter = 0u;
     }
 }
