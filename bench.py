@@ -57,8 +57,12 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--kernels-only", action="store_true")
-    ap.add_argument("--workload", default="c3", choices=["c3", "c4"],
-                    help="c3: 32^3x64 single solve (default); c4: 24^3x48, 16 systems batched")
+    ap.add_argument("--workload", default="c3", choices=["c3", "c4", "c5"],
+                    help="c3: 32^3x64 single solve (default); c4: 24^3x48, 16 systems "
+                         "batched; c5: Poisson stream of solve requests (serving)")
+    ap.add_argument("--requests", type=int, default=2000)
+    ap.add_argument("--load", type=float, default=0.7,
+                    help="c5: offered rate as a fraction of the measured saturation rate")
     ap.add_argument("--nrhs", type=int, default=16)
     ap.add_argument("--reps", type=int, default=3)
     return ap.parse_args()
@@ -342,6 +346,85 @@ def run_c4(args):
 
 
 # ---------------------------------------------------------------------------
+# c5: serving a Poisson stream of solve requests with continuous batching
+# ---------------------------------------------------------------------------
+C5_LATTICES = [((8, 8, 8, 8), 0.4), ((12, 12, 12, 24), 0.3), ((16, 16, 16, 32), 0.2),
+               ((24, 24, 24, 48), 0.1)]
+
+
+def c5_requests(n, rate, seed=2000):
+    """n requests: lattice by weight, one of 2 gauge fields and 4 sources of
+    that lattice, mass log-uniform in [0.005, 0.1], tol 1e-8 or 1e-10, and
+    exponential inter-arrival times of mean 1/rate (rate None: all at 0)."""
+    from paper_1111_0125_gb300.serve import Request
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    w = np.array([p for _, p in C5_LATTICES])
+    lat = rng.choice(len(C5_LATTICES), size=n, p=w / w.sum())
+    gau = rng.integers(2, size=n)
+    src = rng.integers(4, size=n)
+    mass = np.exp(rng.uniform(np.log(0.005), np.log(0.1), size=n))
+    tol = rng.choice([1e-8, 1e-10], size=n)
+    t = np.cumsum(rng.exponential(1.0 / rate, size=n)) if rate else np.zeros(n)
+    return [Request(i, float(t[i]), (int(lat[i]), int(gau[i])), (int(lat[i]), int(src[i])),
+                    float(mass[i]), float(tol[i])) for i in range(n)]
+
+
+def run_c5(args):
+    import numpy as np
+    import torch
+
+    import gen
+    import paper_1111_0125_gb300 as stg
+    from paper_1111_0125_gb300.serve import ServeEngine, summarize
+    torch.cuda.set_device(0)
+    gauges, sources = {}, {}
+    for li, (dims, _) in enumerate(C5_LATTICES):
+        for j in range(2):
+            gauges[(li, j)] = (dims, gen.gauge_field(dims, "exp", seed=10 * li + j, eps=0.5))
+        for j in range(4):
+            sources[(li, j)] = gen.source(dims, seed=1000 + 10 * li + j)
+    sloppy = {"f32": stg.STG_FP32, "fx16": stg.STG_FX16}[args.sloppy]
+    eng = ServeEngine(gauges, sources, hbm_budget=120e9, slots=8, max_sessions_per_gauge=2,
+                      max_resident=8, sloppy=sloppy, recon=args.recon)
+    try:
+        eng.run(c5_requests(64, None, seed=7), realtime=False)       # warm-up, tuning
+        sat_res = eng.run(c5_requests(args.requests, None), realtime=False)
+        sat = summarize(sat_res)
+        rate = args.load * sat["solves_per_s"]
+        clocks = ClockSampler("")
+        res = eng.run(c5_requests(args.requests, rate), realtime=True)
+        ck = clocks.stop()
+    finally:
+        eng.close()
+    summ = summarize(res)
+    per = {}
+    reqs = c5_requests(args.requests, rate)     # the same stream, for per-lattice stats
+    for li, (dims, _) in enumerate(C5_LATTICES):
+        ls = np.array([r.latency for r, q in zip(res, reqs) if q.gauge_key[0] == li])
+        if ls.size:
+            per["x".join(map(str, dims))] = {"n": int(ls.size),
+                                               "p50_ms": 1e3 * float(np.percentile(ls, 50)),
+                                               "p99_ms": 1e3 * float(np.percentile(ls, 99))}
+    print(json.dumps({
+        "metric": METRIC, "workload": "c5: Poisson stream of solve requests, continuous batching",
+        "value": summ["solves_per_s"], "unit": "solves/s", "n_gpus": 1,
+        "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+        "config": {"requests": args.requests, "lattices": {"x".join(map(str, d)): w
+                                                           for d, w in C5_LATTICES},
+                   "gauge_fields": 8, "sources_per_lattice": 4,
+                   "mass": "log-uniform [0.005, 0.1]", "tol": "1e-8 or 1e-10",
+                   "hbm_budget_gb": 120, "slots_per_session": 8, "sessions_per_gauge": 2,
+                   "sloppy_storage": args.sloppy, "offered_rate": rate,
+                   "load_vs_saturation": args.load},
+        "p50_ms": summ["p50_ms"], "p99_ms": summ["p99_ms"], "mean_ms": summ["mean_ms"],
+        "ok": summ["ok"], "saturation": sat, "per_lattice": per,
+        "max_true_res_over_tol": max(r.true_res / q.tol for r, q in zip(res, reqs)),
+        "clocks": ck,
+    }), flush=True)
+
+
+# ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
 def main():
@@ -352,6 +435,9 @@ def main():
         return
     if args.workload == "c4":
         run_c4(args)
+        return
+    if args.workload == "c5":
+        run_c5(args)
         return
     import numpy as np
     import torch

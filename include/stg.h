@@ -270,6 +270,41 @@ stg_status stg_cg_solve_mrhs(const stg_gauge *g, int nrhs, const double *src_dev
                              const double *masses, double tol, const stg_cg_params *params,
                              stg_cg_stats *stats, stg_stream_t stream);
 
+/*
+ * Batch session: the continuous-batching form of stg_cg_solve_mrhs.  A
+ * session owns the device buffers of `max_systems` (1..64) systems on one
+ * gauge handle (it shares the handle's read-only links; several sessions on
+ * one handle may run concurrently on different streams) and runs on `stream`.
+ * Systems join with stg_batch_add and leave when they finish: every
+ * stg_batch_step runs one chunk of inner iterations (params->check_every,
+ * default 16) for all systems present, performs the FP64 reliable updates of
+ * the systems that asked for one, writes x of each finished system and
+ * reports it.  A slot freed by a finished system can take a new system
+ * before the next step, while the other systems continue.
+ *   stg_batch_create: params as for stg_cg_solve (policy RELIABLE or REFINE,
+ *     sloppy FP32 or FX16; NULL = defaults).
+ *   stg_batch_add: src_dev / x_dev canonical complex128 [Vh][3] device fields
+ *     owned by the caller until the system is reported done (x_dev holds x0 on
+ *     entry and the solution after); `slot` receives the system's slot.
+ *     Synchronises the session stream.  STG_ERR_INVALID_ARG when full.
+ *   stg_batch_step: reports up to max_done finished systems (slot, status:
+ *     STG_OK, STG_ERR_NOT_CONVERGED or STG_ERR_BREAKDOWN, and stats; stats may
+ *     be NULL) and the number of systems still present in *n_active.  Returns
+ *     after the chunk's work and any reported solutions are complete.
+ *   stg_batch_bytes: device bytes a session of this size allocates.
+ * The paper solves one system at a time; sessions are this library's
+ * serving layer on top of the batched CG.
+ */
+typedef struct stg_batch stg_batch;
+stg_status stg_batch_create(const stg_gauge *g, int max_systems, const stg_cg_params *params,
+                            stg_stream_t stream, stg_batch **out);
+stg_status stg_batch_destroy(stg_batch *b);
+stg_status stg_batch_add(stg_batch *b, const double *src_dev, double *x_dev, double mass, double tol,
+                         int *slot);
+stg_status stg_batch_step(stg_batch *b, int max_done, int *done_slots, int *done_status,
+                          stg_cg_stats *done_stats, int *n_done, int *n_active);
+size_t stg_batch_bytes(const stg_gauge *g, int max_systems, stg_prec sloppy);
+
 /* The autotuner's choice (rhs_block = NB, threads per block) for this
  * handle's lattice, `prec` and nrhs; STG_ERR_INVALID_ARG if not tuned yet. */
 stg_status stg_mrhs_tuning(const stg_gauge *g, stg_prec prec, int nrhs, int *rhs_block,

@@ -90,6 +90,11 @@ def _load():
         "stg_apply_A_mrhs": (i, [p, i, p, p, p, i, p]),
         "stg_cg_solve_mrhs": (i, [p, i, p, p, p, d, p, p, p]),
         "stg_mrhs_tuning": (i, [p, i, i, p, p]),
+        "stg_batch_create": (i, [p, i, p, p, p]),
+        "stg_batch_destroy": (i, [p]),
+        "stg_batch_add": (i, [p, p, p, d, d, p]),
+        "stg_batch_step": (i, [p, i, p, p, p, p, p]),
+        "stg_batch_bytes": (sz, [p, i, i]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -255,6 +260,42 @@ def stg_cg_solve_mrhs(handle: int, nrhs: int, src_dev, x_dev, masses, tol: float
     out = [s.as_dict() for s in stats]
     _check(st, "stg_cg_solve_mrhs", out)
     return out
+
+
+def stg_batch_create(handle: int, max_systems: int, params=None, stream=None) -> int:
+    """Batch session of up to max_systems systems on one gauge handle."""
+    b = ctypes.c_void_p()
+    pp = ctypes.byref(params) if params is not None else None
+    _check(lib.stg_batch_create(handle, int(max_systems), pp, _stream(stream), ctypes.byref(b)),
+           "stg_batch_create")
+    return b.value
+
+
+def stg_batch_destroy(batch: int) -> None:
+    lib.stg_batch_destroy(batch)
+
+
+def stg_batch_add(batch: int, src_dev, x_dev, mass: float, tol: float) -> int:
+    slot = ctypes.c_int()
+    _check(lib.stg_batch_add(batch, _ptr(src_dev), _ptr(x_dev), float(mass), float(tol),
+                             ctypes.byref(slot)), "stg_batch_add")
+    return slot.value
+
+
+def stg_batch_step(batch: int, max_done: int = 64):
+    """One chunk for every system of the session; returns ([(slot, status,
+    stats), ...] for finished systems, systems still present)."""
+    slots = (ctypes.c_int * max(1, max_done))()
+    status = (ctypes.c_int * max(1, max_done))()
+    stats = (stg_cg_stats * max(1, max_done))()
+    n_done, n_act = ctypes.c_int(), ctypes.c_int()
+    _check(lib.stg_batch_step(batch, int(max_done), slots, status, stats, ctypes.byref(n_done),
+                              ctypes.byref(n_act)), "stg_batch_step")
+    return ([(slots[k], status[k], stats[k].as_dict()) for k in range(n_done.value)], n_act.value)
+
+
+def stg_batch_bytes(handle: int, max_systems: int, sloppy: int) -> int:
+    return int(lib.stg_batch_bytes(handle, int(max_systems), int(sloppy)))
 
 
 def stg_mrhs_tuning(handle: int, prec: int, nrhs: int):

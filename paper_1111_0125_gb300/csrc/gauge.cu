@@ -317,7 +317,7 @@ stg_status workspace_tmp(stg_gauge *g, int prec, void **out)
 void workspace_free(Workspace *ws)
 {
     if (!ws) return;
-    mrhs_free(ws->mrhs);
+    batch_destroy(ws->batch);
     cudaFree(ws->mrhs_tmp);
     for (int k = 0; k < 2; ++k)
         if (ws->graph[k]) cudaGraphExecDestroy(ws->graph[k]);

@@ -173,7 +173,7 @@ static stg_status tune(const stg_gauge *g, const LinkField *lf, int n, const voi
 }
 
 // ---------------------------------------------------------------------------
-// workspace of the multi-system solver
+// device buffers of n systems
 // ---------------------------------------------------------------------------
 static stg_status dev_alloc(void **p, size_t bytes)
 {
@@ -200,18 +200,16 @@ void mrhs_free(MrhsWs *m)
 
 static int pr_of_m(int pd) { return (pd == P16 || pd == PX16) ? P32 : pd; }
 
-static stg_status mrhs_prepare(stg_gauge *g, int n, int pd, MrhsWs **out)
+size_t mrhs_bytes(const Geom &g, int n, int pd)
 {
-    Workspace *ws;
-    STG_TRY(workspace_get(g, &ws));
-    if (ws->mrhs && ws->mrhs->nrhs == n && ws->mrhs->pd == pd) {
-        *out = ws->mrhs;
-        return STG_OK;
-    }
-    if (ws->mrhs) {
-        mrhs_free(ws->mrhs);
-        ws->mrhs = nullptr;
-    }
+    const size_t vh = (size_t)g.Vh;
+    const size_t pstride = (size_t)((g.Vh + 127) / 128) + 64;
+    return n * vh * (3 * 48 + 2 * field_site_bytes(pr_of_m(pd)) + 3 * field_site_bytes(pd)) +
+           vh * 48 + n * pstride * sizeof(double) + n * (sizeof(CGState) + sizeof(int)) + 1024;
+}
+
+static stg_status mrhs_alloc(const stg_gauge *g, int n, int pd, MrhsWs **out)
+{
     MrhsWs *m = new (std::nothrow) MrhsWs();
     if (!m) {
         set_error("multi-system workspace: host allocation failed");
@@ -233,6 +231,7 @@ static stg_status mrhs_prepare(stg_gauge *g, int n, int pd, MrhsWs **out)
     if (st == STG_OK) st = dev_alloc((void **)&m->d, n * m->fd);
     if (st == STG_OK) st = dev_alloc((void **)&m->q, n * m->fd);
     if (st == STG_OK) st = dev_alloc((void **)&m->t, n * m->fd);
+    if (st == STG_OK) st = dev_alloc(&m->tmp, m->f64);  // FP64 odd intermediate
     if (st == STG_OK) st = dev_alloc((void **)&m->partials, n * m->pstride * sizeof(double));
     if (st == STG_OK) st = dev_alloc((void **)&m->states, n * sizeof(CGState));
     if (st == STG_OK) st = dev_alloc((void **)&m->active, (n + 1) * sizeof(int));
@@ -240,23 +239,23 @@ static stg_status mrhs_prepare(stg_gauge *g, int n, int pd, MrhsWs **out)
     if (st == STG_OK) {
         cudaError_t e = cudaMemset(m->states, 0, n * sizeof(CGState));
         if (e == cudaSuccess) e = cudaMemset(m->counter, 0, 256);
+        if (e == cudaSuccess) e = cudaMemset(m->active, 0, (n + 1) * sizeof(int));
         if (e == cudaSuccess) e = cudaMallocHost((void **)&m->states_host, n * sizeof(CGState));
         if (e == cudaSuccess) e = cudaMallocHost((void **)&m->active_host, (n + 1) * sizeof(int));
         if (e != cudaSuccess) st = cuda_fail(e, "multi-system workspace");
     }
-    void *tmp64;
-    if (st == STG_OK) st = workspace_tmp(g, P64, &tmp64);
     if (st != STG_OK) {
         mrhs_free(m);
         return st;
     }
-    ws->mrhs = m;
+    memset(m->states_host, 0, n * sizeof(CGState));
+    memset(m->active_host, 0, (n + 1) * sizeof(int));
     *out = m;
     return STG_OK;
 }
 
 // one iteration of all active systems (4 launches)
-static stg_status iteration_m(stg_gauge *g, MrhsWs *m, const LinkField *lf, cudaStream_t s)
+static stg_status iteration_m(const stg_gauge *g, MrhsWs *m, const LinkField *lf, cudaStream_t s)
 {
     MrhsArgs a = {};
     a.fstride = m->fd;
@@ -282,7 +281,8 @@ static stg_status iteration_m(stg_gauge *g, MrhsWs *m, const LinkField *lf, cuda
                          m->nrhs, s);
 }
 
-static stg_status graph_m(stg_gauge *g, MrhsWs *m, const LinkField *lf, int iters, cudaGraphExec_t *out)
+static stg_status graph_m(const stg_gauge *g, MrhsWs *m, const LinkField *lf, int iters,
+                          cudaGraphExec_t *out)
 {
     if (m->graph && m->graph_iters == iters) {
         *out = m->graph;
@@ -331,208 +331,296 @@ static stg_status sync_states(MrhsWs *m, cudaStream_t s, bool to_host)
     return STG_OK;
 }
 
-enum { SYS_ACTIVE = 0, SYS_DONE = 1, SYS_NOT_CONVERGED = 2, SYS_BREAKDOWN = 3 };
+}  // namespace stg
+
+// ---------------------------------------------------------------------------
+// batch session: systems join and leave between chunks of iterations
+// ---------------------------------------------------------------------------
+struct stg_batch {
+    stg_gauge *g = nullptr;
+    const stg::LinkField *lf = nullptr;
+    int n = 0, pd = 0, pr = 0;
+    stg_cg_params p;
+    cudaStream_t s = nullptr;
+    stg::MrhsWs *m = nullptr;
+    int chunk = 16;
+    long maxiter = 0;
+    bool tuned = false;
+    long launches = 0;
+    struct Slot {
+        int used = 0;              // 1 while the system occupies the slot
+        double bb = 0, rr = 0, tol = 0;
+        long updates = 0;
+        const double *src = nullptr;
+        double *x = nullptr;
+        timespec t_add;
+    };
+    std::vector<Slot> slot;
+    struct Done {
+        int slot;
+        int status;
+        stg_cg_stats stats;
+    };
+    std::vector<Done> pending;   // finished, not yet reported
+};
+
+namespace stg {
+
+static double elapsed_since(const timespec &t0)
+{
+    timespec t1;
+    clock_gettime(CLOCK_MONOTONIC, &t1);
+    return (t1.tv_sec - t0.tv_sec) + 1e-9 * (t1.tv_nsec - t0.tv_nsec);
+}
+
+static void finish(stg_batch *b, int k, int status)
+{
+    stg_batch::Slot &sl = b->slot[k];
+    const CGState &h = b->m->states_host[k];
+    stg_batch::Done d;
+    d.slot = k;
+    d.status = status;
+    memset(&d.stats, 0, sizeof(d.stats));
+    d.stats.iters = (long)h.iter;
+    d.stats.sloppy_iters = (long)h.iter;
+    d.stats.updates = sl.updates;
+    d.stats.true_res = sl.bb > 0.0 ? sqrt(sl.rr / sl.bb) : 0.0;
+    d.stats.iter_res = sl.bb > 0.0 ? sqrt(h.delta_new / sl.bb) : 0.0;
+    d.stats.seconds = elapsed_since(sl.t_add);
+    d.stats.launches = b->launches;
+    b->pending.push_back(d);
+    sl.used = 0;
+}
+
+static void rebuild_active(stg_batch *b)
+{
+    int nact = 0;
+    for (int k = 0; k < b->n; ++k)
+        if (b->slot[k].used) b->m->active_host[1 + nact++] = k;
+    b->m->active_host[0] = nact;
+}
+
+static stg_status push_states(stg_batch *b)
+{
+    MrhsWs *m = b->m;
+    for (int k = 0; k < b->n; ++k) m->states_host[k].counter = 0;
+    STG_TRY(sync_states(m, b->s, false));
+    STG_CUDA(cudaMemcpyAsync(m->active, m->active_host, (b->n + 1) * sizeof(int),
+                             cudaMemcpyHostToDevice, b->s));
+    return STG_OK;
+}
+
+stg_status batch_create(stg_gauge *g, int n, const stg_cg_params *p, cudaStream_t s, stg_batch **out)
+{
+    stg_batch *b = new (std::nothrow) stg_batch();
+    if (!b) {
+        set_error("stg_batch_create: host allocation failed");
+        return STG_ERR_OOM;
+    }
+    b->g = g;
+    b->n = n;
+    b->p = *p;
+    b->pd = p->sloppy;
+    b->pr = pr_of_m(b->pd);
+    b->lf = links_for(g, b->pd);
+    b->s = s;
+    b->maxiter = p->maxiter > 0 ? p->maxiter : 10L * 3L * g->geom.Vh;
+    b->chunk = p->check_every > 0 ? (p->check_every > 256 ? 256 : p->check_every) : 16;
+    b->slot.resize(n);
+    stg_status st = mrhs_alloc(g, n, b->pd, &b->m);
+    if (st != STG_OK) {
+        delete b;
+        return st;
+    }
+    *out = b;
+    return STG_OK;
+}
+
+void batch_destroy(stg_batch *b)
+{
+    if (!b) return;
+    mrhs_free(b->m);
+    delete b;
+}
+
+// Admit one system: b, x0 to FP64, r = b - A x0; the system starts at the
+// next chunk (or is finished at once if x0 already meets the tolerance).
+stg_status batch_add(stg_batch *b, const double *src, double *x, double mass, double tol, int *slot_out)
+{
+    int k = -1;
+    for (int j = 0; j < b->n; ++j)
+        if (!b->slot[j].used) {
+            k = j;
+            break;
+        }
+    if (k < 0) {
+        set_error("stg_batch_add: every slot of the session is occupied");
+        return STG_ERR_INVALID_ARG;
+    }
+    MrhsWs *m = b->m;
+    const Geom &geo = b->g->geom;
+    const int vh = geo.Vh;
+    cudaStream_t s = b->s;
+    stg_batch::Slot &sl = b->slot[k];
+    clock_gettime(CLOCK_MONOTONIC, &sl.t_add);
+    sl.src = src;
+    sl.x = x;
+    sl.tol = tol;
+    sl.updates = 0;
+    STG_TRY(pack_field(geo, P64, src, m->b64 + k * m->f64, s));
+    STG_TRY(pack_field(geo, P64, x, m->x64 + k * m->f64, s));
+    STG_TRY(launch_norm2(P64, vh, m->b64 + k * m->f64, m->states + k, m->partials, s));
+    STG_TRY(sync_states(m, s, true));
+    const double bb = m->states_host[k].result;
+    STG_TRY(launch_true_residual(b->g, m->x64 + k * m->f64, m->b64 + k * m->f64, m->r64 + k * m->f64,
+                                 m->tmp, mass * mass, m->states + k, m->partials, s));
+    STG_TRY(sync_states(m, s, true));
+    const double rr = m->states_host[k].result;
+    b->launches += 5;
+    if (!isfinite(bb) || !isfinite(rr)) {
+        set_error("stg_batch_add: non-finite source or initial residual");
+        return STG_ERR_INVALID_ARG;
+    }
+    sl.bb = bb;
+    sl.rr = rr;
+    sl.used = 1;
+    CGState &h = m->states_host[k];
+    memset(&h, 0, sizeof(CGState));
+    h.m2 = mass * mass;
+    h.stop_r2 = tol * tol * bb;
+    h.trig2 = b->p.policy == STG_CG_PLAIN ? 0.0 : b->p.delta * b->p.delta;
+    h.track_max = (b->p.policy == STG_CG_RELIABLE) ? 1 : 0;
+    h.iter_limit = b->maxiter;
+    h.delta_new = h.delta_old = h.rmax2 = rr;
+    if (bb == 0.0 || rr <= h.stop_r2) {
+        if (bb == 0.0) STG_CUDA(cudaMemsetAsync(x, 0, m->f64, s));
+        h.flag = FLAG_CONVERGED;
+        finish(b, k, STG_OK);
+    } else {
+        STG_TRY(launch_reset(b->pd, vh, m->y + k * m->fr, m->r + k * m->fr, m->d + k * m->fd,
+                             m->r64 + k * m->f64, 0.0, 1, s));
+        ++b->launches;
+        h.flag = FLAG_RUN;
+    }
+    rebuild_active(b);
+    STG_TRY(push_states(b));
+    *slot_out = k;
+    return STG_OK;
+}
+
+// One chunk of iterations for every active system, then the FP64 updates of
+// the systems that asked for one; finished systems get x written.
+stg_status batch_step(stg_batch *b)
+{
+    MrhsWs *m = b->m;
+    if (m->active_host[0] == 0) return STG_OK;
+    const int vh = b->g->geom.Vh;
+    cudaStream_t s = b->s;
+    CGState *h = m->states_host;
+    if (!b->tuned) {
+        // tune NB / block size on the session's own t fields (output only)
+        STG_TRY(tune(b->g, b->lf, b->n, m->d, m->t, m->fd, s, &m->nb, &m->bs));
+        b->tuned = true;
+    }
+    cudaGraphExec_t graph;
+    STG_TRY(graph_m(b->g, m, b->lf, b->chunk, &graph));
+    STG_CUDA(cudaGraphLaunch(graph, s));
+    b->launches += 4L * b->chunk;
+    STG_TRY(sync_states(m, s, true));
+    std::vector<int> flagged;
+    for (int a = 0; a < m->active_host[0]; ++a) {
+        const int k = m->active_host[1 + a];
+        if (h[k].flag != FLAG_RUN) flagged.push_back(k);
+    }
+    if (flagged.empty()) return STG_OK;
+    // Sec. 3.2 updates: x_k += y_k (FP64), r_k = b_k - A_k x_k (FP64)
+    std::vector<CGState> before(flagged.size());
+    for (size_t u = 0; u < flagged.size(); ++u) {
+        const int k = flagged[u];
+        before[u] = h[k];
+        STG_TRY(launch_accumulate_x(b->pr, vh, m->x64 + k * m->f64, m->y + k * m->fr, s));
+        STG_TRY(launch_true_residual(b->g, m->x64 + k * m->f64, m->b64 + k * m->f64,
+                                     m->r64 + k * m->f64, m->tmp, h[k].m2, m->states + k,
+                                     m->partials, s));
+        b->launches += 3;
+        ++b->slot[k].updates;
+    }
+    STG_TRY(sync_states(m, s, true));
+    for (size_t u = 0; u < flagged.size(); ++u) {
+        const int k = flagged[u];
+        const CGState b4 = before[u];
+        const double rr = h[k].result;
+        h[k] = b4;  // the residual kernels touched only result and the counter
+        b->slot[k].rr = rr;
+        int done = -1;
+        if (rr <= h[k].stop_r2) done = STG_OK;
+        else if (!isfinite(rr)) done = STG_ERR_BREAKDOWN;
+        else if (h[k].iter >= b->maxiter) done = STG_ERR_NOT_CONVERGED;
+        if (done >= 0) {
+            STG_TRY(unpack_field(b->g->geom, P64, m->x64 + k * m->f64, b->slot[k].x, s));
+            ++b->launches;
+            h[k].flag = FLAG_CONVERGED;
+            finish(b, k, done);
+            continue;
+        }
+        double beta = 0.0;
+        if (b4.flag != FLAG_BREAKDOWN && b->p.policy == STG_CG_RELIABLE) beta = rr / b4.delta_old;
+        STG_TRY(launch_reset(b->pd, vh, m->y + k * m->fr, m->r + k * m->fr, m->d + k * m->fd,
+                             m->r64 + k * m->f64, beta, 1, s));
+        ++b->launches;
+        h[k].delta_new = rr;
+        h[k].delta_old = rr;
+        h[k].rmax2 = rr;
+        h[k].flag = FLAG_RUN;
+    }
+    rebuild_active(b);
+    STG_TRY(push_states(b));
+    STG_CUDA(cudaStreamSynchronize(s));  // unpacked solutions are complete
+    return STG_OK;
+}
 
 stg_status cg_solve_mrhs(stg_gauge *g, int n, const double *src, double *x, const double *masses,
                          double tol, const stg_cg_params *p, stg_cg_stats *stats, cudaStream_t s)
 {
-    timespec t0, t1;
-    clock_gettime(CLOCK_MONOTONIC, &t0);
-    const Geom &geo = g->geom;
-    const int vh = geo.Vh;
-    const int pd = p->sloppy;
-    const int pr = pr_of_m(pd);
-    const LinkField *lf = links_for(g, pd);
-    MrhsWs *m;
-    STG_TRY(mrhs_prepare(g, n, pd, &m));
-    Workspace *ws = g->ws;
-    const long maxiter = p->maxiter > 0 ? p->maxiter : 10L * 3L * vh;
-    int chunk = p->check_every > 0 ? p->check_every : 16;
-    if (chunk > 256) chunk = 256;
-    const size_t canon = (size_t)vh * 6;  // doubles per canonical field
-
-    std::vector<double> bb(n), rr(n), m2(n);
-    std::vector<int> sys(n, SYS_ACTIVE);
-    std::vector<long> updates(n, 0);
-    long launches = 0;
-    CGState *h = m->states_host;
-
-    // b_k, x0_k into FP64 device layout; |b_k|^2
-    for (int k = 0; k < n; ++k) {
-        m2[k] = masses[k] * masses[k];
-        STG_TRY(pack_field(geo, P64, src + k * canon, m->b64 + k * m->f64, s));
-        STG_TRY(pack_field(geo, P64, x + k * canon, m->x64 + k * m->f64, s));
-        STG_TRY(launch_norm2(P64, vh, m->b64 + k * m->f64, m->states + k, m->partials, s));
-        launches += 3;
+    // one cached session per handle for this convenience call
+    Workspace *ws;
+    STG_TRY(workspace_get(g, &ws));
+    stg_batch *b = ws->batch;
+    if (b && (b->n != n || b->pd != p->sloppy)) {
+        batch_destroy(b);
+        ws->batch = b = nullptr;
     }
-    STG_TRY(sync_states(m, s, true));
-    for (int k = 0; k < n; ++k) {
-        bb[k] = h[k].result;
-        if (!isfinite(bb[k])) {
-            set_error("stg_cg_solve_mrhs: a source has non-finite entries");
-            return STG_ERR_INVALID_ARG;
-        }
+    if (!b) {
+        STG_TRY(batch_create(g, n, p, s, &b));
+        ws->batch = b;
     }
-    // r_k = b_k - A_k x0_k
-    for (int k = 0; k < n; ++k) {
-        STG_TRY(launch_true_residual(g, m->x64 + k * m->f64, m->b64 + k * m->f64, m->r64 + k * m->f64,
-                                     ws->tmp[P64], m2[k], m->states + k, m->partials, s));
-        launches += 2;
-    }
-    STG_TRY(sync_states(m, s, true));
-    int nact = 0;
-    for (int k = 0; k < n; ++k) {
-        rr[k] = h[k].result;
-        const double stop = tol * tol * bb[k];
-        memset(&h[k], 0, sizeof(CGState));
-        h[k].m2 = m2[k];
-        h[k].stop_r2 = stop;
-        h[k].trig2 = p->policy == STG_CG_PLAIN ? 0.0 : p->delta * p->delta;
-        h[k].track_max = (p->policy == STG_CG_RELIABLE) ? 1 : 0;
-        h[k].iter_limit = maxiter;
-        h[k].delta_new = h[k].delta_old = h[k].rmax2 = rr[k];
-        if (bb[k] == 0.0 || rr[k] <= stop) {
-            sys[k] = SYS_DONE;
-            h[k].flag = FLAG_CONVERGED;
-            if (bb[k] == 0.0) STG_CUDA(cudaMemsetAsync(m->x64 + k * m->f64, 0, m->f64, s));
-            continue;
-        }
-        // y = 0, r = r64, d = r (Fig. 1 / Fig. 2 start)
-        STG_TRY(launch_reset(pd, vh, m->y + k * m->fr, m->r + k * m->fr, m->d + k * m->fd,
-                             m->r64 + k * m->f64, 0.0, 1, s));
-        ++launches;
-        h[k].flag = FLAG_RUN;
-        m->active_host[1 + nact++] = k;
-    }
-    m->active_host[0] = nact;
-    STG_TRY(sync_states(m, s, false));
-    STG_CUDA(cudaMemcpyAsync(m->active, m->active_host, (n + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
-
-    stg_status status = STG_OK;
-    if (nact > 0) {
-        // tune NB / BS on the solver's own fields (their values are reset below)
-        status = tune(g, lf, n, m->d, m->t, m->fd, s, &m->nb, &m->bs);
-        if (status == STG_OK && m->tuned_nb != m->nb) {
-            if (m->graph) cudaGraphExecDestroy(m->graph);
-            m->graph = nullptr;
-            m->tuned_nb = m->nb;
-        }
-        // the tuner wrote t only; d still holds r
-        cudaGraphExec_t graph = nullptr;
-        if (status == STG_OK) status = graph_m(g, m, lf, chunk, &graph);
-        while (status == STG_OK && nact > 0) {
-            cudaError_t e = cudaGraphLaunch(graph, s);
-            if (e != cudaSuccess) {
-                status = cuda_fail(e, "cudaGraphLaunch");
-                break;
-            }
-            launches += 4L * chunk;
-            status = sync_states(m, s, true);
-            if (status != STG_OK) break;
-            // systems that raised a flag: x += y, r = b - A x in FP64
-            std::vector<int> flagged;
-            for (int a = 0; a < nact; ++a) {
-                const int k = m->active_host[1 + a];
-                if (h[k].flag != FLAG_RUN) flagged.push_back(k);
-            }
-            if (flagged.empty()) continue;
-            std::vector<CGState> before(flagged.size());
-            for (size_t u = 0; u < flagged.size(); ++u) {
-                const int k = flagged[u];
-                before[u] = h[k];
-                if (pd != P64) {
-                    status = launch_accumulate_x(pr, vh, m->x64 + k * m->f64, m->y + k * m->fr, s);
-                    if (status != STG_OK) break;
-                }
-                status = launch_true_residual(g, m->x64 + k * m->f64, m->b64 + k * m->f64,
-                                              m->r64 + k * m->f64, ws->tmp[P64], m2[k], m->states + k,
-                                              m->partials, s);
-                if (status != STG_OK) break;
-                launches += 3;
-                ++updates[k];
-            }
-            if (status != STG_OK) break;
-            status = sync_states(m, s, true);
-            if (status != STG_OK) break;
-            for (size_t u = 0; u < flagged.size(); ++u) {
-                const int k = flagged[u];
-                const CGState &b4 = before[u];
-                rr[k] = h[k].result;
-                // restore the iterate's scalars (the residual kernels only
-                // touched result and the counter)
-                h[k] = b4;
-                if (rr[k] <= h[k].stop_r2) {
-                    sys[k] = SYS_DONE;
-                    h[k].flag = FLAG_CONVERGED;
-                    continue;
-                }
-                if (!isfinite(rr[k])) {
-                    sys[k] = SYS_BREAKDOWN;
-                    continue;
-                }
-                if (h[k].iter >= maxiter) {
-                    sys[k] = SYS_NOT_CONVERGED;
-                    continue;
-                }
-                double beta = 0.0;
-                if (b4.flag != FLAG_BREAKDOWN && p->policy == STG_CG_RELIABLE) beta = rr[k] / b4.delta_old;
-                status = launch_reset(pd, vh, m->y + k * m->fr, m->r + k * m->fr, m->d + k * m->fd,
-                                      m->r64 + k * m->f64, beta, 1, s);
-                if (status != STG_OK) break;
-                ++launches;
-                h[k].delta_new = rr[k];
-                h[k].delta_old = rr[k];
-                h[k].rmax2 = rr[k];
-                h[k].flag = FLAG_RUN;
-            }
-            if (status != STG_OK) break;
-            nact = 0;
-            for (int k = 0; k < n; ++k)
-                if (sys[k] == SYS_ACTIVE) m->active_host[1 + nact++] = k;
-            m->active_host[0] = nact;
-            for (int k = 0; k < n; ++k) h[k].counter = 0;
-            status = sync_states(m, s, false);
-            if (status != STG_OK) break;
-            e = cudaMemcpyAsync(m->active, m->active_host, (n + 1) * sizeof(int), cudaMemcpyHostToDevice, s);
-            if (e != cudaSuccess) status = cuda_fail(e, "cudaMemcpyAsync(active)");
-        }
-    }
-    if (status == STG_OK) {
-        for (int k = 0; k < n && status == STG_OK; ++k) {
-            status = unpack_field(geo, P64, m->x64 + k * m->f64, x + k * canon, s);
-            ++launches;
-        }
-        cudaError_t e = cudaStreamSynchronize(s);
-        if (status == STG_OK && e != cudaSuccess) status = cuda_fail(e, "cudaStreamSynchronize");
-    }
-    clock_gettime(CLOCK_MONOTONIC, &t1);
-    const double secs = (t1.tv_sec - t0.tv_sec) + 1e-9 * (t1.tv_nsec - t0.tv_nsec);
-    bool not_conv = false, broke = false;
-    for (int k = 0; k < n; ++k) {
+    b->p = *p;
+    b->s = s;
+    b->launches = 0;
+    b->maxiter = p->maxiter > 0 ? p->maxiter : 10L * 3L * g->geom.Vh;
+    b->chunk = p->check_every > 0 ? (p->check_every > 256 ? 256 : p->check_every) : 16;
+    b->pending.clear();
+    const size_t canon = (size_t)g->geom.Vh * 6;
+    std::vector<int> slot_of(n, -1);
+    for (int k = 0; k < n; ++k) STG_TRY(batch_add(b, src + k * canon, x + k * canon, masses[k], tol, &slot_of[k]));
+    while (b->m->active_host[0] > 0) STG_TRY(batch_step(b));
+    STG_CUDA(cudaStreamSynchronize(s));
+    stg_status worst = STG_OK;
+    for (const stg_batch::Done &d : b->pending) {
+        int k = -1;
+        for (int j = 0; j < n; ++j)
+            if (slot_of[j] == d.slot) k = j;
+        if (k < 0) continue;
         if (stats) {
-            stg_cg_stats &o = stats[k];
-            memset(&o, 0, sizeof(o));
-            o.iters = (long)h[k].iter;
-            o.sloppy_iters = (long)h[k].iter;
-            o.updates = updates[k];
-            o.true_res = bb[k] > 0.0 ? sqrt(rr[k] / bb[k]) : 0.0;
-            o.iter_res = bb[k] > 0.0 ? sqrt(h[k].delta_new / bb[k]) : 0.0;
-            o.seconds = secs;
-            o.launches = launches;
+            stats[k] = d.stats;
+            stats[k].launches = b->launches;
         }
-        not_conv |= sys[k] == SYS_NOT_CONVERGED;
-        broke |= sys[k] == SYS_BREAKDOWN;
+        if (d.status != STG_OK && worst == STG_OK) worst = (stg_status)d.status;
     }
-    if (status != STG_OK) return status;
-    if (broke) {
-        set_error("stg_cg_solve_mrhs: non-finite true residual in a system");
-        return STG_ERR_BREAKDOWN;
-    }
-    if (not_conv) {
-        set_error("stg_cg_solve_mrhs: maxiter reached before convergence of a system");
-        return STG_ERR_NOT_CONVERGED;
-    }
-    return STG_OK;
+    b->pending.clear();
+    if (worst == STG_ERR_BREAKDOWN) set_error("stg_cg_solve_mrhs: non-finite true residual in a system");
+    if (worst == STG_ERR_NOT_CONVERGED) set_error("stg_cg_solve_mrhs: maxiter reached before convergence of a system");
+    return worst;
 }
 
 }  // namespace stg
@@ -673,6 +761,84 @@ stg_status stg_cg_solve_mrhs(const stg_gauge *gc, int nrhs, const double *src_de
     stg_gauge *g = const_cast<stg_gauge *>(gc);
     DevScope ds(g->device);
     return cg_solve_mrhs(g, nrhs, src_dev, x_dev, masses, tol, &p, stats, (cudaStream_t)stream);
+}
+
+stg_status stg_batch_create(const stg_gauge *gc, int max_systems, const stg_cg_params *params,
+                            stg_stream_t stream, stg_batch **out)
+{
+    if (!gc || !out || max_systems < 1 || max_systems > kMaxRhs) {
+        set_error("stg_batch_create: NULL argument or max_systems outside [1, 64]");
+        return STG_ERR_INVALID_ARG;
+    }
+    stg_cg_params p;
+    if (params) p = *params;
+    else stg_cg_params_default(gc, &p);
+    if (p.policy < STG_CG_RELIABLE || p.policy > STG_CG_REFINE || !(p.delta > 0.0 && p.delta < 1.0) ||
+        p.maxiter < 0 || p.check_every < 0) {
+        set_error("stg_batch_create: bad params (policy RELIABLE or REFINE, 0 < delta < 1)");
+        return STG_ERR_INVALID_ARG;
+    }
+    const LinkField *lf;
+    STG_TRY(check_m(gc, max_systems, p.sloppy, &lf));
+    stg_gauge *g = const_cast<stg_gauge *>(gc);
+    DevScope ds(g->device);
+    *out = nullptr;
+    return batch_create(g, max_systems, &p, (cudaStream_t)stream, out);
+}
+
+stg_status stg_batch_destroy(stg_batch *b)
+{
+    if (!b) return STG_OK;
+    DevScope ds(b->g->device);
+    cudaStreamSynchronize(b->s);
+    batch_destroy(b);
+    return STG_OK;
+}
+
+stg_status stg_batch_add(stg_batch *b, const double *src_dev, double *x_dev, double mass, double tol,
+                         int *slot)
+{
+    if (!b || !src_dev || !x_dev || !slot || src_dev == x_dev) {
+        set_error("stg_batch_add: NULL argument or src == x");
+        return STG_ERR_INVALID_ARG;
+    }
+    if (!isfinite(mass) || mass < 0.0 || !isfinite(tol) || !(tol > 0.0)) {
+        set_error("stg_batch_add: mass must be finite and >= 0, tol finite and > 0");
+        return STG_ERR_INVALID_ARG;
+    }
+    DevScope ds(b->g->device);
+    return batch_add(b, src_dev, x_dev, mass, tol, slot);
+}
+
+stg_status stg_batch_step(stg_batch *b, int max_done, int *done_slots, int *done_status,
+                          stg_cg_stats *done_stats, int *n_done, int *n_active)
+{
+    if (!b || max_done < 0 || (max_done > 0 && (!done_slots || !done_status)) || !n_done) {
+        set_error("stg_batch_step: bad argument");
+        return STG_ERR_INVALID_ARG;
+    }
+    DevScope ds(b->g->device);
+    *n_done = 0;
+    stg_status st = STG_OK;
+    if (b->pending.empty()) st = batch_step(b);
+    int k = 0;
+    while (k < max_done && !b->pending.empty()) {
+        const stg_batch::Done d = b->pending.front();
+        b->pending.erase(b->pending.begin());
+        done_slots[k] = d.slot;
+        done_status[k] = d.status;
+        if (done_stats) done_stats[k] = d.stats;
+        ++k;
+    }
+    *n_done = k;
+    if (n_active) *n_active = b->m->active_host[0] + (int)b->pending.size();
+    return st;
+}
+
+size_t stg_batch_bytes(const stg_gauge *g, int max_systems, stg_prec sloppy)
+{
+    if (!g || max_systems < 1) return 0;
+    return mrhs_bytes(g->geom, max_systems, sloppy);
 }
 
 stg_status stg_mrhs_tuning(const stg_gauge *g, stg_prec prec, int nrhs, int *rhs_block, int *threads)

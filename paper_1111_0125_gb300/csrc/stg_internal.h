@@ -40,6 +40,8 @@ struct MrhsWs {
     int nb = 1, bs = 256, tuned_nb = -1;
 };
 void mrhs_free(MrhsWs *m);
+void batch_destroy(stg_batch *b);
+size_t mrhs_bytes(const Geom &g, int n, int pd);
 
 }  // namespace stg
 
@@ -91,7 +93,7 @@ struct Workspace {
     int graph_sloppy[2] = {-1, -1}, graph_iters[2] = {0, 0};
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // per-kernel events
     cudaEvent_t ev_chunk[2] = {nullptr, nullptr};                        // around plain chunks
-    MrhsWs *mrhs = nullptr;           // multi-system solver
+    stg_batch *batch = nullptr;       // session cached for stg_cg_solve_mrhs
     void *mrhs_tmp = nullptr;         // odd intermediates of stg_apply_A_mrhs
     size_t mrhs_tmp_bytes = 0;
 };

@@ -1,0 +1,290 @@
+"""Serving loop: a stream of solve requests with continuous batching.
+
+Requests (lattice, gauge field, mass, tolerance, source) arrive over time.
+Each resident gauge field has batch sessions (``stg_batch_*``): a session
+holds the device state of up to `slots` systems and advances all of them by
+one chunk of CG iterations per step; between steps finished systems leave
+and newly arrived requests take their slots, so requests that arrive while
+others are on the GPU join the running batch instead of waiting for it to
+drain.  Every session runs on its own CUDA stream in its own host thread
+(the C calls release the GIL), so sessions of different gauge fields and
+lattices overlap on the device.
+
+Admission is by an HBM budget: a gauge field is uploaded (at most
+`max_resident` at a time, least recently used idle one evicted) and a
+session created only while the budget allows; otherwise the request waits
+until memory frees.  Latency is measured per request from its arrival to the
+moment its solution is back in host memory.
+
+This module only schedules: every solve runs in the CUDA library through the
+C ABI.
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import threading
+import time
+
+import numpy as np
+import torch
+
+from . import (STG_FP32, STG_OK, stg_batch_add, stg_batch_bytes, stg_batch_create,
+               stg_batch_destroy, stg_batch_step, stg_cg_params_default)
+from .fields import Gauge
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    arrival: float          # seconds after the start of the stream
+    gauge_key: object       # key into the gauge table
+    source_key: object      # key into the source table
+    mass: float
+    tol: float
+
+
+@dataclasses.dataclass
+class Result:
+    rid: int
+    arrival: float
+    done: float
+    status: int
+    iters: int
+    updates: int
+    true_res: float
+    x: np.ndarray | None
+
+    @property
+    def latency(self) -> float:
+        return self.done - self.arrival
+
+
+def gauge_bytes(dims, recon: int = 12, sloppy_link_bytes: int = 48) -> int:
+    """Device bytes of a handle: FP64/18 links plus the sloppy links."""
+    v = int(np.prod(dims))
+    return v // 2 * 8 * (144 + sloppy_link_bytes) + 4096
+
+
+class _Session:
+    """One batch session on one resident gauge field, driven by a thread."""
+
+    def __init__(self, engine, entry, device):
+        self.engine = engine
+        self.entry = entry
+        self.stream = torch.cuda.Stream(device=device)
+        params = stg_cg_params_default(entry.gauge.handle)
+        params.sloppy = engine.sloppy
+        params.check_every = engine.chunk
+        self.handle = stg_batch_create(entry.gauge.handle, engine.slots, params, self.stream)
+        self.bytes = stg_batch_bytes(entry.gauge.handle, engine.slots, engine.sloppy)
+        self.vh = entry.gauge.vh
+        self.device = device
+        self.busy = {}            # slot -> (request, source buffer, solution buffer)
+        self.inbox = collections.deque()
+        self.cv = threading.Condition()
+        self.stop = False
+        self.thread = threading.Thread(target=self._run, daemon=True)
+        self.thread.start()
+
+    def load(self) -> int:
+        with self.cv:
+            return len(self.busy) + len(self.inbox)
+
+    def free_slots(self) -> int:
+        return self.engine.slots - self.load()
+
+    def submit(self, req: Request):
+        with self.cv:
+            self.inbox.append(req)
+            self.cv.notify()
+
+    def close(self):
+        with self.cv:
+            self.stop = True
+            self.cv.notify()
+        self.thread.join()
+        stg_batch_destroy(self.handle)
+
+    def _admit(self, req: Request):
+        host = self.engine.sources[req.source_key]
+        with torch.cuda.stream(self.stream):
+            # buffers live until the system is reported done (stream-ordered
+            # caching allocator on the session stream)
+            src = torch.empty((self.vh, 3), dtype=torch.complex128, device=self.device)
+            src.copy_(host, non_blocking=True)
+            x = torch.zeros_like(src)
+        slot = stg_batch_add(self.handle, src, x, req.mass, req.tol)
+        self.busy[slot] = (req, src, x)
+
+    def _run(self):
+        torch.cuda.set_device(self.engine.device)
+        eng = self.engine
+        while True:
+            with self.cv:
+                while not self.stop and not self.inbox and not self.busy:
+                    self.cv.wait()
+                if self.stop and not self.busy and not self.inbox:
+                    return
+                new = []
+                while self.inbox and len(self.busy) + len(new) < eng.slots:
+                    new.append(self.inbox.popleft())
+            for req in new:
+                self._admit(req)
+            done, _ = stg_batch_step(self.handle, eng.slots)
+            for slot, status, st in done:
+                req, src, x = self.busy.pop(slot)
+                with torch.cuda.stream(self.stream):
+                    xh = x.to("cpu", non_blocking=True)
+                self.stream.synchronize()
+                eng._complete(req, status, st, xh.numpy() if eng.keep_solutions else None)
+            if done:
+                eng._wake()
+
+
+@dataclasses.dataclass
+class _GaugeEntry:
+    key: object
+    gauge: Gauge
+    bytes: int
+    sessions: list
+    last_used: float
+
+
+class ServeEngine:
+    """Continuous-batching solve server on one GPU.
+
+    gauges:  key -> (dims, canonical host links)
+    sources: key -> canonical host source (complex128 [Vh][3]); pinned on entry
+    """
+
+    def __init__(self, gauges: dict, sources: dict, hbm_budget: float = 120e9, slots: int = 8,
+                 max_sessions_per_gauge: int = 2, max_resident: int = 8, sloppy: int = STG_FP32,
+                 recon: int = 12, chunk: int = 16, keep_solutions: bool = False, device: int = 0):
+        self.gauge_src = gauges
+        self.sources = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory()
+                        for k, v in sources.items()}
+        self.budget = float(hbm_budget)
+        self.slots = int(slots)
+        self.max_sessions = int(max_sessions_per_gauge)
+        self.max_resident = int(max_resident)
+        self.sloppy = sloppy
+        self.recon = recon
+        self.chunk = chunk
+        self.keep_solutions = keep_solutions
+        self.device = device
+        self.used = 0.0
+        self.resident: dict = {}
+        self.results: list = []
+        self.lock = threading.Lock()
+        self.event = threading.Event()
+        self.t0 = None
+        torch.cuda.set_device(device)
+        self.upload_stream = torch.cuda.Stream(device=device)
+
+    # -- bookkeeping called from session threads --------------------------
+    def _complete(self, req, status, st, x):
+        t = time.perf_counter() - self.t0
+        with self.lock:
+            self.results.append(Result(req.rid, req.arrival, t, status, st["iters"],
+                                       st["updates"], st["true_res"], x))
+
+    def _wake(self):
+        self.event.set()
+
+    # -- placement ----------------------------------------------------------
+    def _gauge(self, key):
+        e = self.resident.get(key)
+        if e is not None:
+            return e
+        dims, links = self.gauge_src[key]
+        need = gauge_bytes(dims)
+        # evict idle gauges while over the resident count or the budget
+        while (len(self.resident) >= self.max_resident or self.used + need > self.budget):
+            idle = [g for g in self.resident.values() if all(s.load() == 0 for s in g.sessions)]
+            if not idle:
+                return None
+            victim = min(idle, key=lambda g: g.last_used)
+            self._evict(victim)
+        g = Gauge(dims, links, sloppy=self.sloppy, recon=self.recon, stream=self.upload_stream)
+        e = _GaugeEntry(key, g, need, [], time.perf_counter())
+        self.resident[key] = e
+        self.used += need
+        return e
+
+    def _evict(self, e):
+        for s in e.sessions:
+            s.close()
+            self.used -= s.bytes
+        e.gauge.close()
+        self.used -= e.bytes
+        del self.resident[e.key]
+
+    def _place(self, req) -> bool:
+        e = self._gauge(req.gauge_key)
+        if e is None:
+            return False
+        e.last_used = time.perf_counter()
+        open_s = [s for s in e.sessions if s.free_slots() > 0]
+        if open_s:
+            min(open_s, key=lambda s: s.load()).submit(req)
+            return True
+        if len(e.sessions) < self.max_sessions:
+            need = stg_batch_bytes(e.gauge.handle, self.slots, self.sloppy) + \
+                2 * self.slots * e.gauge.vh * 48
+            if self.used + need <= self.budget:
+                s = _Session(self, e, self.device)
+                self.used += s.bytes
+                e.sessions.append(s)
+                s.submit(req)
+                return True
+        return False
+
+    # -- the stream -----------------------------------------------------------
+    def run(self, requests, realtime: bool = True):
+        """Serve `requests` (sorted by arrival).  realtime=False submits every
+        request at once (saturation run).  Returns the results by rid."""
+        torch.cuda.set_device(self.device)
+        self.results = []
+        pending = collections.deque()
+        todo = collections.deque(sorted(requests, key=lambda r: r.arrival))
+        self.t0 = time.perf_counter()
+        n = len(todo)
+        while True:
+            now = time.perf_counter() - self.t0
+            while todo and (not realtime or todo[0].arrival <= now):
+                r = todo.popleft()
+                if not realtime:
+                    r.arrival = now
+                pending.append(r)
+            still = collections.deque()
+            while pending:
+                r = pending.popleft()
+                if not self._place(r):
+                    still.append(r)
+            pending = still
+            with self.lock:
+                finished = len(self.results)
+            if finished == n:
+                break
+            wait = 0.05
+            if todo and realtime:
+                wait = min(wait, max(0.0, todo[0].arrival - (time.perf_counter() - self.t0)))
+            self.event.wait(wait)
+            self.event.clear()
+        return sorted(self.results, key=lambda r: r.rid)
+
+    def close(self):
+        for e in list(self.resident.values()):
+            self._evict(e)
+
+
+def summarize(results, makespan=None) -> dict:
+    lat = np.array([r.latency for r in results])
+    span = makespan if makespan is not None else max(r.done for r in results) - min(
+        r.arrival for r in results)
+    ok = sum(1 for r in results if r.status == STG_OK)
+    return {"requests": len(results), "ok": ok, "solves_per_s": len(results) / span,
+            "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+            "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+            "mean_ms": 1e3 * float(lat.mean()), "makespan_s": span}
