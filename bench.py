@@ -150,7 +150,7 @@ def measured_hbm():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("dslash.cu", "stg_common.cuh"):
+    for f in ("dslash.cu", "dslash_fx16.cu", "stg_common.cuh"):
         with open(os.path.join(ROOT, "paper_1111_0125_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
