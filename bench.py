@@ -318,7 +318,7 @@ def run_c4(args):
     s1.synchronize()
     t_m = s0.elapsed_time(s1) / 20
     L, S = LINK_BYTES[(args.sloppy, args.recon)], FIELD_BYTES[args.sloppy]
-    nbytes = vh * (8 * L * -(-n // nb) + 2 * S * n)
+    nbytes = vh * (8 * L * -(-n // (nb * tb)) + 2 * S * n)   # links once per NB x TPS systems
     peak, src_ = measured_hbm()
     achieved = nbytes / (t_m / 1000.0) / 1e9
     print(json.dumps({
@@ -335,7 +335,7 @@ def run_c4(args):
         "iters": [s_["iters"] for s_ in st], "updates": [s_["updates"] for s_ in st],
         "true_res_max": max(s_["true_res"] for s_ in st),
         "iters_one_by_one": [s_["iters"] for s_ in single],
-        "mrhs_dslash": {"rhs_block": nb, "threads": tb, "launch_ms": t_m,
+        "mrhs_dslash": {"rhs_block": nb, "threads_per_site": tb, "launch_ms": t_m,
                         "algorithmic_bytes_per_launch": nbytes,
                         "bytes_per_site_per_system": nbytes / vh / n,
                         "achieved": achieved, "peak": peak, "peak_source": src_, "unit": "GB/s",

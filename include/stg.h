@@ -305,10 +305,11 @@ stg_status stg_batch_step(stg_batch *b, int max_done, int *done_slots, int *done
                           stg_cg_stats *done_stats, int *n_done, int *n_active);
 size_t stg_batch_bytes(const stg_gauge *g, int max_systems, stg_prec sloppy);
 
-/* The autotuner's choice (rhs_block = NB, threads per block) for this
- * handle's lattice, `prec` and nrhs; STG_ERR_INVALID_ARG if not tuned yet. */
+/* The autotuner's choice (rhs_block = NB systems per thread and block,
+ * threads_per_site = TPS) for this handle's lattice, `prec` and nrhs;
+ * STG_ERR_INVALID_ARG if not tuned yet. */
 stg_status stg_mrhs_tuning(const stg_gauge *g, stg_prec prec, int nrhs, int *rhs_block,
-                           int *threads);
+                           int *threads_per_site);
 
 /* Fill params with the defaults: RELIABLE, sloppy = handle's sloppy
  * precision, delta = 0.1, maxiter = 0 (10 N_dim), check_every = 0 (auto),

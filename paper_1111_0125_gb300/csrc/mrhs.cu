@@ -25,16 +25,18 @@
 
 namespace stg {
 
-void launch_dslash_m_f32(int recon, int nb, int bs, int epi, const MrhsArgs &a, cudaStream_t s);
-void launch_dslash_m_fx16(int recon, int nb, int bs, int epi, const MrhsArgs &a, cudaStream_t s);
+void launch_dslash_m_f32_12(int shape, int epi, const MrhsArgs &a, cudaStream_t s);
+void launch_dslash_m_f32_18(int shape, int epi, const MrhsArgs &a, cudaStream_t s);
+void launch_dslash_m_fx16_12(int shape, int epi, const MrhsArgs &a, cudaStream_t s);
+void launch_dslash_m_fx16_18(int shape, int epi, const MrhsArgs &a, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // autotuner cache: process-wide, optionally mirrored in a text file named by
-// the STG_TUNE_CACHE environment variable ("Lx Ly Lz Lt prec recon n nb bs")
+// the STG_TUNE_CACHE environment variable ("Lx Ly Lz Lt prec recon n shape")
 // ---------------------------------------------------------------------------
 struct TuneEntry {
     int dims[4];
-    int prec, recon, nrhs, nb, bs;
+    int prec, recon, nrhs, shape;
 };
 
 static std::mutex g_tune_mutex;
@@ -47,10 +49,7 @@ static bool same_key(const TuneEntry &e, const int *dims, int prec, int recon, i
            e.dims[3] == dims[3] && e.prec == prec && e.recon == recon && e.nrhs == nrhs;
 }
 
-static bool valid_choice(int nb, int bs)
-{
-    return (nb == 1 || nb == 2 || nb == 4 || nb == 8) && (bs == 128 || bs == 256);
-}
+static bool valid_choice(int shape) { return shape >= 0 && shape < kMrhsShapes; }
 
 static void tune_load_file_locked()
 {
@@ -61,53 +60,67 @@ static void tune_load_file_locked()
     FILE *f = fopen(path, "r");
     if (!f) return;
     TuneEntry e;
-    while (fscanf(f, "%d %d %d %d %d %d %d %d %d", &e.dims[0], &e.dims[1], &e.dims[2], &e.dims[3],
-                  &e.prec, &e.recon, &e.nrhs, &e.nb, &e.bs) == 9) {
-        if (valid_choice(e.nb, e.bs)) g_tune.push_back(e);
+    while (fscanf(f, "%d %d %d %d %d %d %d %d", &e.dims[0], &e.dims[1], &e.dims[2], &e.dims[3],
+                  &e.prec, &e.recon, &e.nrhs, &e.shape) == 8) {
+        if (valid_choice(e.shape)) g_tune.push_back(e);
     }
     fclose(f);
 }
 
-static bool tune_lookup(const int *dims, int prec, int recon, int nrhs, int *nb, int *bs)
+static bool tune_lookup(const int *dims, int prec, int recon, int nrhs, int *shape)
 {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     tune_load_file_locked();
     for (const TuneEntry &e : g_tune)
         if (same_key(e, dims, prec, recon, nrhs)) {
-            *nb = e.nb;
-            *bs = e.bs;
+            *shape = e.shape;
             return true;
         }
     return false;
 }
 
-static void tune_store(const int *dims, int prec, int recon, int nrhs, int nb, int bs)
+static void tune_store(const int *dims, int prec, int recon, int nrhs, int shape)
 {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
-    TuneEntry e = {{dims[0], dims[1], dims[2], dims[3]}, prec, recon, nrhs, nb, bs};
+    TuneEntry e = {{dims[0], dims[1], dims[2], dims[3]}, prec, recon, nrhs, shape};
     g_tune.push_back(e);
     const char *path = getenv("STG_TUNE_CACHE");
     if (!path || !*path) return;
     FILE *f = fopen(path, "a");
     if (!f) return;
-    fprintf(f, "%d %d %d %d %d %d %d %d %d\n", dims[0], dims[1], dims[2], dims[3], prec, recon,
-            nrhs, nb, bs);
+    fprintf(f, "%d %d %d %d %d %d %d %d\n", dims[0], dims[1], dims[2], dims[3], prec, recon, nrhs,
+            shape);
     fclose(f);
+}
+
+static int num_sms_m()
+{
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+            n = 148;
+    }
+    return n;
 }
 
 // ---------------------------------------------------------------------------
 // launches
 // ---------------------------------------------------------------------------
-static stg_status launch_m(const stg_gauge *g, const LinkField *lf, int nb, int bs, int epi,
-                           MrhsArgs &a, cudaStream_t s)
+static stg_status launch_m(const stg_gauge *g, const LinkField *lf, int shape, int epi, MrhsArgs &a,
+                           cudaStream_t s)
 {
     a.g = g->geom;
+    a.grid_cap = 2 * num_sms_m();  // blocks resident at 128 registers; they stride over tiles
     for (int mu = 0; mu < 4; ++mu) {
         a.lf[mu] = lf->blk(a.parity, mu);
         a.lb[mu] = lf->blk(1 - a.parity, mu);
     }
-    if (lf->prec == P32) launch_dslash_m_f32(lf->recon, nb, bs, epi, a, s);
-    else if (lf->prec == PX16) launch_dslash_m_fx16(lf->recon, nb, bs, epi, a, s);
+    if (lf->prec == P32 && lf->recon == 12) launch_dslash_m_f32_12(shape, epi, a, s);
+    else if (lf->prec == P32) launch_dslash_m_f32_18(shape, epi, a, s);
+    else if (lf->prec == PX16 && lf->recon == 12) launch_dslash_m_fx16_12(shape, epi, a, s);
+    else if (lf->prec == PX16) launch_dslash_m_fx16_18(shape, epi, a, s);
     else {
         set_error("multi-system Dslash: only FP32 and FX16 storage are supported");
         return STG_ERR_UNSUPPORTED;
@@ -116,13 +129,13 @@ static stg_status launch_m(const stg_gauge *g, const LinkField *lf, int nb, int 
     return STG_OK;
 }
 
-// Time one EPI_NONE half-pass of all n systems for every (NB, BS) candidate
-// (one warm-up and three timed launches each, CUDA events on `s`) and keep
-// the fastest.  `in` / `out` hold n fields each and are overwritten.
+// Time one EPI_NONE half-pass of all n systems for every (NB, threads per
+// site) shape with TPS <= n (one warm-up and three timed launches each, CUDA
+// events on `s`) and keep the fastest.  `out` (n fields) is overwritten.
 static stg_status tune(const stg_gauge *g, const LinkField *lf, int n, const void *in, void *out,
-                       size_t fstride, cudaStream_t s, int *nb_out, int *bs_out)
+                       size_t fstride, cudaStream_t s, int *shape_out)
 {
-    if (tune_lookup(g->dims, lf->prec, lf->recon, n, nb_out, bs_out)) return STG_OK;
+    if (tune_lookup(g->dims, lf->prec, lf->recon, n, shape_out)) return STG_OK;
     cudaEvent_t e0, e1;
     STG_CUDA(cudaEventCreate(&e0));
     cudaError_t ce = cudaEventCreate(&e1);
@@ -131,44 +144,38 @@ static stg_status tune(const stg_gauge *g, const LinkField *lf, int n, const voi
         return cuda_fail(ce, "cudaEventCreate");
     }
     float best = 1e30f;
-    int bnb = 1, bbs = 256;
+    int bshape = 0;
     stg_status st = STG_OK;
-    const int nbs[4] = {1, 2, 4, 8};
-    const int bss[2] = {128, 256};
-    for (int u = 0; u < 4 && st == STG_OK; ++u) {
-        if (nbs[u] > 1 && nbs[u] > n) break;
-        for (int v = 0; v < 2 && st == STG_OK; ++v) {
-            MrhsArgs a = {};
-            a.parity = 1;
-            a.in = static_cast<const char *>(in);
-            a.out = static_cast<char *>(out);
-            a.fstride = fstride;
-            a.nrhs = n;
-            st = launch_m(g, lf, nbs[u], bss[v], EPI_NONE, a, s);
-            if (st != STG_OK) break;
-            cudaEventRecord(e0, s);
-            for (int r = 0; r < 3 && st == STG_OK; ++r) st = launch_m(g, lf, nbs[u], bss[v], EPI_NONE, a, s);
-            cudaEventRecord(e1, s);
-            ce = cudaEventSynchronize(e1);
-            float ms = 0.f;
-            if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
-            if (ce != cudaSuccess) {
-                st = cuda_fail(ce, "autotune timing");
-                break;
-            }
-            if (ms < best) {
-                best = ms;
-                bnb = nbs[u];
-                bbs = bss[v];
-            }
+    for (int k = 0; k < kMrhsShapes && st == STG_OK; ++k) {
+        if (mrhs_tps(k) > n || (mrhs_tps(k) == 1 && mrhs_nb(k) > n && mrhs_nb(k) > 1)) continue;
+        MrhsArgs a = {};
+        a.parity = 1;
+        a.in = static_cast<const char *>(in);
+        a.out = static_cast<char *>(out);
+        a.fstride = fstride;
+        a.nrhs = n;
+        st = launch_m(g, lf, k, EPI_NONE, a, s);
+        if (st != STG_OK) break;
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < 3 && st == STG_OK; ++r) st = launch_m(g, lf, k, EPI_NONE, a, s);
+        cudaEventRecord(e1, s);
+        ce = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+        if (ce != cudaSuccess) {
+            st = cuda_fail(ce, "autotune timing");
+            break;
+        }
+        if (ms < best) {
+            best = ms;
+            bshape = k;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st != STG_OK) return st;
-    tune_store(g->dims, lf->prec, lf->recon, n, bnb, bbs);
-    *nb_out = bnb;
-    *bs_out = bbs;
+    tune_store(g->dims, lf->prec, lf->recon, n, bshape);
+    *shape_out = bshape;
     return STG_OK;
 }
 
@@ -203,7 +210,7 @@ static int pr_of_m(int pd) { return (pd == P16 || pd == PX16) ? P32 : pd; }
 size_t mrhs_bytes(const Geom &g, int n, int pd)
 {
     const size_t vh = (size_t)g.Vh;
-    const size_t pstride = (size_t)((g.Vh + 127) / 128) + 64;
+    const size_t pstride = (size_t)((g.Vh + 127) / 128) + 1024;
     return n * vh * (3 * 48 + 2 * field_site_bytes(pr_of_m(pd)) + 3 * field_site_bytes(pd)) +
            vh * 48 + n * pstride * sizeof(double) + n * (sizeof(CGState) + sizeof(int)) + 1024;
 }
@@ -221,7 +228,7 @@ static stg_status mrhs_alloc(const stg_gauge *g, int n, int pd, MrhsWs **out)
     m->f64 = vh * 48;
     m->fr = vh * field_site_bytes(pr_of_m(pd));
     m->fd = vh * field_site_bytes(pd);
-    m->pstride = (size_t)((g->geom.Vh + 127) / 128) + 64;
+    m->pstride = (size_t)((g->geom.Vh + 127) / 128) + 1024;  // >= both grids of the iteration
     stg_status st = STG_OK;
     char **bufs[] = {&m->x64, &m->b64, &m->r64};
     for (char **b : bufs)
@@ -268,12 +275,12 @@ static stg_status iteration_m(const stg_gauge *g, MrhsWs *m, const LinkField *lf
     a.parity = 1;
     a.in = m->d;
     a.out = m->t;
-    STG_TRY(launch_m(g, lf, m->nb, m->bs, EPI_GATE, a, s));
+    STG_TRY(launch_m(g, lf, m->shape, EPI_GATE, a, s));
     a.parity = 0;
     a.in = m->t;
     a.out = m->q;
     a.w = m->d;
-    STG_TRY(launch_m(g, lf, m->nb, m->bs, EPI_A_CG, a, s));
+    STG_TRY(launch_m(g, lf, m->shape, EPI_A_CG, a, s));
     const int vh = g->geom.Vh;
     STG_TRY(launch_update_m(m->pd, vh, m->y, m->r, m->d, m->q, m->fr, m->fd, m->states, m->partials,
                             m->pstride, m->active + 1, m->active, m->nrhs, s));
@@ -519,7 +526,7 @@ stg_status batch_step(stg_batch *b)
     CGState *h = m->states_host;
     if (!b->tuned) {
         // tune NB / block size on the session's own t fields (output only)
-        STG_TRY(tune(b->g, b->lf, b->n, m->d, m->t, m->fd, s, &m->nb, &m->bs));
+        STG_TRY(tune(b->g, b->lf, b->n, m->d, m->t, m->fd, s, &m->shape));
         b->tuned = true;
     }
     cudaGraphExec_t graph;
@@ -671,15 +678,15 @@ stg_status stg_dslash_mrhs(const stg_gauge *g, int out_parity, int nrhs, const v
     DevScope ds(g->device);
     cudaStream_t s = (cudaStream_t)stream;
     const size_t fb = (size_t)g->geom.Vh * field_site_bytes(prec);
-    int nb, bs;
-    STG_TRY(tune(g, lf, nrhs, in_dev, out_dev, fb, s, &nb, &bs));
+    int shape;
+    STG_TRY(tune(g, lf, nrhs, in_dev, out_dev, fb, s, &shape));
     MrhsArgs a = {};
     a.parity = out_parity;
     a.in = static_cast<const char *>(in_dev);
     a.out = static_cast<char *>(out_dev);
     a.fstride = fb;
     a.nrhs = nrhs;
-    return launch_m(g, lf, nb, bs, EPI_NONE, a, s);
+    return launch_m(g, lf, shape, EPI_NONE, a, s);
 }
 
 stg_status stg_apply_A_mrhs(const stg_gauge *gc, int nrhs, const double *masses, const void *in_dev,
@@ -709,21 +716,21 @@ stg_status stg_apply_A_mrhs(const stg_gauge *gc, int nrhs, const double *masses,
         STG_TRY(dev_alloc(&ws->mrhs_tmp, nrhs * fb));
         ws->mrhs_tmp_bytes = nrhs * fb;
     }
-    int nb, bs;
-    STG_TRY(tune(g, lf, nrhs, in_dev, ws->mrhs_tmp, fb, s, &nb, &bs));
+    int shape;
+    STG_TRY(tune(g, lf, nrhs, in_dev, ws->mrhs_tmp, fb, s, &shape));
     MrhsArgs a = {};
     a.parity = 1;
     a.in = static_cast<const char *>(in_dev);
     a.out = static_cast<char *>(ws->mrhs_tmp);
     a.fstride = fb;
     a.nrhs = nrhs;
-    STG_TRY(launch_m(g, lf, nb, bs, EPI_NONE, a, s));
+    STG_TRY(launch_m(g, lf, shape, EPI_NONE, a, s));
     a.parity = 0;
     a.in = static_cast<const char *>(ws->mrhs_tmp);
     a.out = static_cast<char *>(out_dev);
     a.w = static_cast<const char *>(in_dev);
     for (int k = 0; k < nrhs; ++k) a.m2[k] = (float)(masses[k] * masses[k]);
-    return launch_m(g, lf, nb, bs, EPI_A, a, s);
+    return launch_m(g, lf, shape, EPI_A, a, s);
 }
 
 stg_status stg_cg_solve_mrhs(const stg_gauge *gc, int nrhs, const double *src_dev, double *x_dev,
@@ -841,18 +848,22 @@ size_t stg_batch_bytes(const stg_gauge *g, int max_systems, stg_prec sloppy)
     return mrhs_bytes(g->geom, max_systems, sloppy);
 }
 
-stg_status stg_mrhs_tuning(const stg_gauge *g, stg_prec prec, int nrhs, int *rhs_block, int *threads)
+stg_status stg_mrhs_tuning(const stg_gauge *g, stg_prec prec, int nrhs, int *rhs_block,
+                           int *threads_per_site)
 {
     const LinkField *lf;
     STG_TRY(check_m(g, nrhs, prec, &lf));
-    if (!rhs_block || !threads) {
+    if (!rhs_block || !threads_per_site) {
         set_error("stg_mrhs_tuning: NULL output");
         return STG_ERR_INVALID_ARG;
     }
-    if (!tune_lookup(g->dims, lf->prec, lf->recon, nrhs, rhs_block, threads)) {
+    int shape;
+    if (!tune_lookup(g->dims, lf->prec, lf->recon, nrhs, &shape)) {
         set_error("stg_mrhs_tuning: not tuned yet for this lattice, precision and nrhs");
         return STG_ERR_INVALID_ARG;
     }
+    *rhs_block = mrhs_nb(shape);
+    *threads_per_site = mrhs_tps(shape);
     return STG_OK;
 }
 

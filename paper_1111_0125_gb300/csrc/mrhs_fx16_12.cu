@@ -1,0 +1,11 @@
+// Multi-system Dslash instantiations: FX16 storage, 12-real links.
+#include "mrhs_kernels.cuh"
+
+namespace stg {
+
+void launch_dslash_m_fx16_12(int shape, int epi, const MrhsArgs &a, cudaStream_t s)
+{
+    launch_m_pr<PX16, 12>(shape, epi, a, s);
+}
+
+}  // namespace stg

@@ -5,8 +5,9 @@
 // sides in register blocks of NB: the site's eight links are loaded (and
 // decoded / rebuilt) once per block and applied to NB input fields, so the
 // link bytes per site and right-hand side fall from 8L to 8L / NB while the
-// field bytes stay 2S (3S with the fused epilogue).  NB and the block size BS
-// are template parameters picked by the autotuner in mrhs.cu.
+// field bytes stay 2S (3S with the fused epilogue).  With TPS threads per
+// site the register block covers NB x TPS systems per link load.  (NB, TPS)
+// comes from the autotuner in mrhs.cu.
 //
 // The right-hand sides processed are those of a device-side list (active,
 // nactive) so that the host can drop converged systems between chunks
@@ -38,16 +39,37 @@ struct MrhsArgs {
     float m2[kMaxRhs];     // EPI_A: m_k^2
     float2 *partials;      // EPI_A_CG: [nrhs][gridDim.x]
     unsigned *counter;     // EPI_A_CG: arrival counter
+    int grid_cap;          // blocks launched at most (they stride over site tiles)
 };
 
-template <int P, int R, int NB, int EPI, int BS>
-__global__ void __launch_bounds__(BS) k_dslash_m(const MrhsArgs a)
+constexpr int kMrhsBlock = 256;
+
+// TPS threads share one site (consecutive lanes of a warp): they load the
+// same link words, which the load unit merges into one request, so the
+// links come from DRAM once per site for all systems; lane `sub` of the
+// group handles systems sub, sub + TPS, ... in register blocks of NB.
+template <int P, int R, int NB, int TPS, int EPI>
+__global__ void __launch_bounds__(kMrhsBlock) k_dslash_m(const MrhsArgs a)
 {
+    constexpr int BS = kMrhsBlock;
     typedef typename Real<P>::T T;
     const int vh = a.g.Vh;
-    const int i = blockIdx.x * BS + threadIdx.x;
-    const bool ok = i < vh;
+    const int sub = threadIdx.x % TPS;
     const int nact = a.active ? *a.nactive : a.nrhs;
+    const int per = (nact + TPS - 1) / TPS;  // systems per lane (uniform bound)
+    constexpr int kTile = BS / TPS;          // sites per tile
+    const int ntiles = (vh + kTile - 1) / kTile;
+
+    __shared__ float2 red[NB][TPS][BS / 32];
+    __shared__ FF sys_acc[kMaxRhs];          // this block's d^dag q per list slot
+    if (EPI == EPI_A_CG) {
+        for (int k = threadIdx.x; k < kMaxRhs; k += BS) sys_acc[k].hi = sys_acc[k].lo = 0.f;
+        __syncthreads();
+    }
+
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int i = tile * kTile + threadIdx.x / TPS;
+    const bool ok = i < vh;
 
     int jf[4] = {0, 0, 0, 0}, jb[4] = {0, 0, 0, 0};
     T s2f[4], s2b[4];
@@ -67,13 +89,12 @@ __global__ void __launch_bounds__(BS) k_dslash_m(const MrhsArgs a)
         }
     }
 
-    __shared__ float2 red[NB][BS / 32];
-    for (int k0 = 0; k0 < nact; k0 += NB) {
+    for (int k0 = 0; k0 < per; k0 += NB) {
         int rid[NB];
         bool run[NB];
 #pragma unroll
         for (int q = 0; q < NB; ++q) {
-            const int kk = k0 + q;
+            const int kk = sub + TPS * (k0 + q);
             run[q] = kk < nact;
             rid[q] = run[q] ? (a.active ? a.active[kk] : kk) : 0;
             if (EPI == EPI_GATE || EPI == EPI_A_CG)
@@ -88,22 +109,22 @@ __global__ void __launch_bounds__(BS) k_dslash_m(const MrhsArgs a)
 #pragma unroll
         for (int q = 0; q < NB; ++q) dot[q].hi = dot[q].lo = 0.f;
         if (ok) {
+            // No branches in the hot loop: a slot that is not running reads
+            // system rid = 0 (valid memory) and its result is dropped below,
+            // so every load of the NB systems can issue before the math.
 #pragma unroll
             for (int mu = 0; mu < 4; ++mu) {
                 const Mat3<T> uf = LinkIO<P, R>::load(a.lf[mu], vh, i);
+                Vec3<T> v[NB];
 #pragma unroll
-                for (int q = 0; q < NB; ++q)
-                    if (run[q]) {
-                        const Vec3<T> v = FieldIO<P>::load_nc(a.in + rid[q] * a.fstride, vh, jf[mu]);
-                        mul_add(uf, v, acc[q], s2f[mu]);
-                    }
+                for (int q = 0; q < NB; ++q) v[q] = FieldIO<P>::load_nc(a.in + rid[q] * a.fstride, vh, jf[mu]);
+#pragma unroll
+                for (int q = 0; q < NB; ++q) mul_add(uf, v[q], acc[q], s2f[mu]);
                 const Mat3<T> ub = LinkIO<P, R>::load(a.lb[mu], vh, jb[mu]);
 #pragma unroll
-                for (int q = 0; q < NB; ++q)
-                    if (run[q]) {
-                        const Vec3<T> v = FieldIO<P>::load_nc(a.in + rid[q] * a.fstride, vh, jb[mu]);
-                        adj_mul_sub(ub, v, acc[q], s2b[mu]);
-                    }
+                for (int q = 0; q < NB; ++q) v[q] = FieldIO<P>::load_nc(a.in + rid[q] * a.fstride, vh, jb[mu]);
+#pragma unroll
+                for (int q = 0; q < NB; ++q) adj_mul_sub(ub, v[q], acc[q], s2b[mu]);
             }
 #pragma unroll
             for (int q = 0; q < NB; ++q) {
@@ -136,34 +157,43 @@ __global__ void __launch_bounds__(BS) k_dslash_m(const MrhsArgs a)
             }
         }
         if (EPI == EPI_A_CG) {
-            // per-system block partials: warp sums, then one pass over warps
+            // lanes holding the same system (equal sub) are TPS apart: shuffle
+            // down to offset TPS only, then add the warps into sys_acc
             const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
             for (int q = 0; q < NB; ++q) {
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) dot[q] = ff_add(dot[q], ff_shfl_down(dot[q], o));
-                if (lane == 0) red[q][w] = make_float2(dot[q].hi, dot[q].lo);
+                for (int o = 16; o >= TPS; o >>= 1) dot[q] = ff_add(dot[q], ff_shfl_down(dot[q], o));
+                if (lane < TPS) red[q][lane][w] = make_float2(dot[q].hi, dot[q].lo);
             }
             __syncthreads();
-            if ((int)threadIdx.x < NB && k0 + (int)threadIdx.x < nact) {
-                // system of slot threadIdx.x, recomputed (no dynamic register indexing)
-                const int kk = k0 + threadIdx.x;
-                const int k = a.active ? a.active[kk] : kk;
-                if (a.states[k].flag == FLAG_RUN) {
-                    FF s = {0.f, 0.f};
+            if ((int)threadIdx.x < NB * TPS) {
+                const int q = threadIdx.x / TPS, sb = threadIdx.x % TPS;
+                const int kk = sb + TPS * (k0 + q);
+                if (kk < nact) {
+                    FF sum = sys_acc[kk];
 #pragma unroll
                     for (int ww = 0; ww < BS / 32; ++ww) {
                         FF t;
-                        t.hi = red[threadIdx.x][ww].x;
-                        t.lo = red[threadIdx.x][ww].y;
-                        s = ff_add(s, t);
+                        t.hi = red[q][sb][ww].x;
+                        t.lo = red[q][sb][ww].y;
+                        sum = ff_add(sum, t);
                     }
-                    a.partials[(size_t)k * gridDim.x + blockIdx.x] = make_float2(s.hi, s.lo);
-                    __threadfence();
+                    sys_acc[kk] = sum;
                 }
             }
             __syncthreads();
         }
+    }
+    }  // tiles
+
+    if (EPI == EPI_A_CG) {
+        for (int kk = threadIdx.x; kk < nact; kk += BS) {
+            const int k = a.active ? a.active[kk] : kk;
+            a.partials[(size_t)k * gridDim.x + blockIdx.x] = make_float2(sys_acc[kk].hi, sys_acc[kk].lo);
+        }
+        __threadfence();
+        __syncthreads();
     }
 
     if (EPI == EPI_A_CG) {
@@ -204,30 +234,44 @@ __global__ void __launch_bounds__(BS) k_dslash_m(const MrhsArgs a)
     }
 }
 
-// Launch one (P, R) family: picks the NB / BS instantiation at run time.
-template <int P, int R>
-void launch_m_pr(int nb, int bs, int epi, const MrhsArgs &a, cudaStream_t s)
+// (NB, TPS) shapes the autotuner chooses from
+constexpr int kMrhsShapes = 9;
+__host__ __device__ constexpr int mrhs_nb(int k)
 {
-#define STG_M_EPI(NB_, BS_)                                                                      \
-    do {                                                                                         \
-        const int grid = (a.g.Vh + BS_ - 1) / BS_;                                               \
-        switch (epi) {                                                                           \
-        case EPI_NONE: k_dslash_m<P, R, NB_, EPI_NONE, BS_><<<grid, BS_, 0, s>>>(a); break;      \
-        case EPI_A: k_dslash_m<P, R, NB_, EPI_A, BS_><<<grid, BS_, 0, s>>>(a); break;            \
-        case EPI_GATE: k_dslash_m<P, R, NB_, EPI_GATE, BS_><<<grid, BS_, 0, s>>>(a); break;      \
-        case EPI_A_CG: k_dslash_m<P, R, NB_, EPI_A_CG, BS_><<<grid, BS_, 0, s>>>(a); break;      \
-        }                                                                                        \
+    return k == 0 ? 1 : k == 1 ? 2 : k == 2 ? 4 : k == 3 ? 2 : k == 4 ? 1 : k == 5 ? 2 : k == 6 ? 1 : k == 7 ? 2 : 1;
+}
+__host__ __device__ constexpr int mrhs_tps(int k)
+{
+    return k == 0 ? 1 : k == 1 ? 1 : k == 2 ? 1 : k == 3 ? 2 : k == 4 ? 4 : k == 5 ? 4 : k == 6 ? 8 : k == 7 ? 8 : 16;
+}
+
+// Launch one (P, R) family with the shape index `shape` (0..kMrhsShapes-1).
+template <int P, int R>
+void launch_m_pr(int shape, int epi, const MrhsArgs &a, cudaStream_t s)
+{
+#define STG_M_EPI(K_)                                                                                  \
+    do {                                                                                               \
+        constexpr int NB_ = mrhs_nb(K_), TPS_ = mrhs_tps(K_);                                           \
+        const long tiles_ = ((long)a.g.Vh * TPS_ + kMrhsBlock - 1) / kMrhsBlock;                      \
+        const int grid = (int)(tiles_ < a.grid_cap ? tiles_ : a.grid_cap);                             \
+        switch (epi) {                                                                                 \
+        case EPI_NONE: k_dslash_m<P, R, NB_, TPS_, EPI_NONE><<<grid, kMrhsBlock, 0, s>>>(a); break;    \
+        case EPI_A: k_dslash_m<P, R, NB_, TPS_, EPI_A><<<grid, kMrhsBlock, 0, s>>>(a); break;          \
+        case EPI_GATE: k_dslash_m<P, R, NB_, TPS_, EPI_GATE><<<grid, kMrhsBlock, 0, s>>>(a); break;    \
+        case EPI_A_CG: k_dslash_m<P, R, NB_, TPS_, EPI_A_CG><<<grid, kMrhsBlock, 0, s>>>(a); break;    \
+        }                                                                                              \
     } while (0)
-#define STG_M_NB(BS_)                                  \
-    do {                                               \
-        if (nb == 1) STG_M_EPI(1, BS_);                \
-        else if (nb == 2) STG_M_EPI(2, BS_);           \
-        else if (nb == 4) STG_M_EPI(4, BS_);           \
-        else STG_M_EPI(8, BS_);                        \
-    } while (0)
-    if (bs == 128) STG_M_NB(128);
-    else STG_M_NB(256);
-#undef STG_M_NB
+    switch (shape) {
+    case 0: STG_M_EPI(0); break;
+    case 1: STG_M_EPI(1); break;
+    case 2: STG_M_EPI(2); break;
+    case 3: STG_M_EPI(3); break;
+    case 4: STG_M_EPI(4); break;
+    case 5: STG_M_EPI(5); break;
+    case 6: STG_M_EPI(6); break;
+    case 7: STG_M_EPI(7); break;
+    default: STG_M_EPI(8); break;
+    }
 #undef STG_M_EPI
 }
 

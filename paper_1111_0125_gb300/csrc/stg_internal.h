@@ -37,7 +37,7 @@ struct MrhsWs {
     void *tmp = nullptr;
     cudaGraphExec_t graph = nullptr;
     int graph_iters = 0;
-    int nb = 1, bs = 256, tuned_nb = -1;
+    int shape = 0;                    // autotuned (NB, threads per site) index
 };
 void mrhs_free(MrhsWs *m);
 void batch_destroy(stg_batch *b);

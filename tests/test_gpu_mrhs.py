@@ -57,8 +57,8 @@ def test_dslash_mrhs_matches_oracle_and_single(dims, prec, recon, n):
                 # same products; the compiler may contract them into FMAs
                 # differently in the two kernels, so agreement is to rounding
                 assert rel(got[k], single) < TOL[prec]
-        nb, bs = stg.stg_mrhs_tuning(g.handle, prec, n)
-        assert nb in (1, 2, 4, 8) and nb <= max(1, n) and bs in (128, 256)
+        nb, tps = stg.stg_mrhs_tuning(g.handle, prec, n)
+        assert nb in (1, 2, 4) and tps in (1, 2, 4, 8, 16) and tps <= max(1, n)
 
 
 @pytest.mark.parametrize("prec", [stg.STG_FP32, stg.STG_FX16])
