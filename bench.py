@@ -52,7 +52,8 @@ def parse():
     ap.add_argument("--mass", type=float, default=0.005)
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--eps", type=float, default=0.6)
-    ap.add_argument("--delta", type=float, default=0.1)
+    ap.add_argument("--delta", type=float, default=None,
+                    help="reliable-update threshold (default: the library's per-precision default)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 CG comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -271,7 +272,9 @@ def run_c4(args):
     g = stg.Gauge(dims, U, sloppy=sloppy, recon=args.recon)
     stream = torch.cuda.current_stream()
     src = torch.from_numpy(np.ascontiguousarray(bs)).to(dev)
-    p = g.params(policy=stg.STG_CG_RELIABLE, sloppy=sloppy, delta=args.delta)
+    p = g.params(policy=stg.STG_CG_RELIABLE, sloppy=sloppy)
+    if args.delta is not None:
+        p.delta = args.delta
 
     def batched():
         x = torch.zeros_like(src)
@@ -472,7 +475,10 @@ def main():
             print(json.dumps({"kernels_only": True, "lattice": dims, "reps": args.reps}))
         return
 
-    params = g.params(policy=stg.STG_CG_RELIABLE, sloppy=sloppy, delta=args.delta, timing=1)
+    params = g.params(policy=stg.STG_CG_RELIABLE, sloppy=sloppy, timing=1)
+    if args.delta is not None:
+        params.delta = args.delta
+    args.delta = params.delta
 
     def solve():
         x = torch.zeros_like(b)

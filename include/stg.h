@@ -312,7 +312,8 @@ stg_status stg_mrhs_tuning(const stg_gauge *g, stg_prec prec, int nrhs, int *rhs
                            int *threads_per_site);
 
 /* Fill params with the defaults: RELIABLE, sloppy = handle's sloppy
- * precision, delta = 0.1, maxiter = 0 (10 N_dim), check_every = 0 (auto),
+ * precision, delta = 0.05 for FP32, 0.25 for FP16 / FX16 inner iterations
+ * (0.1 without a handle), maxiter = 0 (10 N_dim), check_every = 0 (auto),
  * timing = 0. */
 stg_status stg_cg_params_default(const stg_gauge *g, stg_cg_params *params);
 
