@@ -140,6 +140,8 @@ template <int PD, int PR>
 __global__ void __launch_bounds__(kBlock, kVecBlocksPerSM)
 k_cg_update(int vh, void *y, void *r, const void *d, const void *q, CGState *st, double *partials)
 {
+    pdl_wait();
+    pdl_trigger();
     cg_update_body<PD, PR>(vh, y, r, d, q, st, partials);
 }
 
@@ -196,6 +198,8 @@ template <int PD, int PR>
 __global__ void __launch_bounds__(kBlock, kVecBlocksPerSM)
 k_xpay(int vh, const void *r, void *d, const CGState *st)
 {
+    pdl_wait();
+    pdl_trigger();
     xpay_body<PD, PR>(vh, r, d, st);
 }
 
@@ -308,6 +312,16 @@ static int pr_of(int pd) { return (pd == P16 || pd == PX16) ? P32 : pd; }
         else KERNEL<PX16, P32><<<grid, kBlock, 0, s>>>(__VA_ARGS__);                         \
     } while (0)
 
+#define STG_DISPATCH_PD_EX(pd, KERNEL, PDL, ...)                                             \
+    do {                                                                                     \
+        cudaError_t e_;                                                                      \
+        if ((pd) == P64) e_ = launch_k(KERNEL<P64, P64>, grid, kBlock, 0, s, PDL, __VA_ARGS__);  \
+        else if ((pd) == P32) e_ = launch_k(KERNEL<P32, P32>, grid, kBlock, 0, s, PDL, __VA_ARGS__); \
+        else if ((pd) == P16) e_ = launch_k(KERNEL<P16, P32>, grid, kBlock, 0, s, PDL, __VA_ARGS__); \
+        else e_ = launch_k(KERNEL<PX16, P32>, grid, kBlock, 0, s, PDL, __VA_ARGS__);              \
+        STG_CUDA(e_);                                                                        \
+    } while (0)
+
 static stg_status norm2(const Geom &g, int prec, const void *v, Workspace *ws, cudaStream_t s)
 {
     const int grid = grid_for(g.Vh);
@@ -332,6 +346,10 @@ static stg_status iteration(stg_gauge *gg, Workspace *ws, int pd, cudaStream_t s
     L.state = ws->state;
     L.partials = ws->partials;
     L.counter = &ws->state->counter;
+    // without per-kernel events, consecutive kernels overlap by programmatic
+    // dependent launch (each waits for its predecessor before reading)
+    const bool pdl = ev == nullptr;
+    L.pdl = pdl;
     if (ev) STG_CUDA(cudaEventRecordWithFlags(ev[0], s, cudaEventRecordExternal));
     // the state flag gates every kernel, including the first half-pass
     L.out_parity = 1;
@@ -346,9 +364,9 @@ static stg_status iteration(stg_gauge *gg, Workspace *ws, int pd, cudaStream_t s
     STG_TRY(launch_dslash(g, pd, EPI_A_CG, L, s));
     if (ev) STG_CUDA(cudaEventRecordWithFlags(ev[2], s, cudaEventRecordExternal));
     const int grid = grid_vec(g.Vh, pr_of(pd));
-    STG_DISPATCH_PD(pd, k_cg_update, g.Vh, ws->y, ws->r, ws->d, ws->q, ws->state, ws->partials);
+    STG_DISPATCH_PD_EX(pd, k_cg_update, pdl, g.Vh, ws->y, ws->r, ws->d, ws->q, ws->state, ws->partials);
     if (ev) STG_CUDA(cudaEventRecordWithFlags(ev[3], s, cudaEventRecordExternal));
-    STG_DISPATCH_PD(pd, k_xpay, g.Vh, ws->r, ws->d, ws->state);
+    STG_DISPATCH_PD_EX(pd, k_xpay, pdl, g.Vh, ws->r, ws->d, ws->state);
     if (ev) STG_CUDA(cudaEventRecordWithFlags(ev[4], s, cudaEventRecordExternal));
     STG_CUDA(cudaGetLastError());
     return STG_OK;
@@ -694,6 +712,11 @@ stg_status cg_solve(stg_gauge *g, const double *src, double *x, double mass, dou
             }
             const int flag = h->flag;
             if (flag == FLAG_RUN) continue;
+            if (flag == FLAG_TIMEOUT) {
+                set_error("stg_cg_solve: a bounded wait inside the Dslash kernel gave up");
+                status = STG_ERR_TIMEOUT;
+                break;
+            }
             // Sec. 3.2 update: x_{k+1} = x_k + y_n (FP64), r_{k+1} = b - A x_{k+1}
             if (!plain) {
                 if (pr == P64) k_accumulate_x<P64><<<grid, kBlock, 0, s>>>(geo.Vh, ws->x64, ws->y);

@@ -29,6 +29,8 @@ template <int P, int R, int EPI>
 __global__ void __launch_bounds__(kBlock) k_dslash(const DslashArgs a)
 {
     typedef typename Real<P>::T T;
+    pdl_wait();
+    pdl_trigger();
     if (EPI == EPI_A_CG || EPI == EPI_GATE) {
         if (a.state->flag != FLAG_RUN) return;  // uniform over the grid
     }
@@ -117,15 +119,15 @@ __global__ void __launch_bounds__(kBlock) k_dslash(const DslashArgs a)
 }
 
 template <int P, int R>
-static void launch_pr(int epi, const DslashArgs &a, int grid, cudaStream_t s)
+static void launch_pr(int epi, const DslashArgs &a, int grid, cudaStream_t s, bool pdl)
 {
     switch (epi) {
-    case EPI_NONE: k_dslash<P, R, EPI_NONE><<<grid, kBlock, 0, s>>>(a); break;
-    case EPI_A: k_dslash<P, R, EPI_A><<<grid, kBlock, 0, s>>>(a); break;
-    case EPI_A_DOT: k_dslash<P, R, EPI_A_DOT><<<grid, kBlock, 0, s>>>(a); break;
-    case EPI_A_CG: k_dslash<P, R, EPI_A_CG><<<grid, kBlock, 0, s>>>(a); break;
-    case EPI_RES: k_dslash<P, R, EPI_RES><<<grid, kBlock, 0, s>>>(a); break;
-    case EPI_GATE: k_dslash<P, R, EPI_GATE><<<grid, kBlock, 0, s>>>(a); break;
+    case EPI_NONE: launch_k(k_dslash<P, R, EPI_NONE>, grid, kBlock, 0, s, pdl, a); break;
+    case EPI_A: launch_k(k_dslash<P, R, EPI_A>, grid, kBlock, 0, s, pdl, a); break;
+    case EPI_A_DOT: launch_k(k_dslash<P, R, EPI_A_DOT>, grid, kBlock, 0, s, pdl, a); break;
+    case EPI_A_CG: launch_k(k_dslash<P, R, EPI_A_CG>, grid, kBlock, 0, s, pdl, a); break;
+    case EPI_RES: launch_k(k_dslash<P, R, EPI_RES>, grid, kBlock, 0, s, pdl, a); break;
+    case EPI_GATE: launch_k(k_dslash<P, R, EPI_GATE>, grid, kBlock, 0, s, pdl, a); break;
     }
 }
 
@@ -138,6 +140,7 @@ stg_status launch_dslash(const Geom &g, int prec, int epi, const DslashLaunch &L
         a.lf[mu] = L.links->blk(L.out_parity, mu);
         a.lb[mu] = L.links->blk(1 - L.out_parity, mu);
     }
+    a.lt = L.links->tiled ? L.links->tiled + (size_t)L.out_parity * L.links->tiled_parity_bytes : nullptr;
     a.in = L.in;
     a.out = L.out;
     a.w = L.w;
@@ -154,19 +157,19 @@ stg_status launch_dslash(const Geom &g, int prec, int epi, const DslashLaunch &L
         return STG_ERR_UNSUPPORTED;
     }
     if (prec == PX16) {  // two sites per thread on packed FP32x2 (dslash_fx16.cu)
-        launch_dslash_fx2(recon, epi, a, s);
+        launch_dslash_fx2(recon, epi, a, s, L.pdl);
         STG_CUDA(cudaGetLastError());
         return STG_OK;
     }
     if (prec == P64) {
-        if (recon == 18) launch_pr<P64, 18>(epi, a, grid, s);
-        else launch_pr<P64, 12>(epi, a, grid, s);
+        if (recon == 18) launch_pr<P64, 18>(epi, a, grid, s, L.pdl);
+        else launch_pr<P64, 12>(epi, a, grid, s, L.pdl);
     } else if (prec == P32) {
-        if (recon == 18) launch_pr<P32, 18>(epi, a, grid, s);
-        else launch_pr<P32, 12>(epi, a, grid, s);
+        if (recon == 18) launch_pr<P32, 18>(epi, a, grid, s, L.pdl);
+        else launch_pr<P32, 12>(epi, a, grid, s, L.pdl);
     } else {
-        if (recon == 18) launch_pr<P16, 18>(epi, a, grid, s);
-        else launch_pr<P16, 12>(epi, a, grid, s);
+        if (recon == 18) launch_pr<P16, 18>(epi, a, grid, s, L.pdl);
+        else launch_pr<P16, 12>(epi, a, grid, s, L.pdl);
     }
     STG_CUDA(cudaGetLastError());
     return STG_OK;

@@ -16,6 +16,8 @@
 // (32767 U); the sum is scaled by 1/32767 at the end, and the 12-real row 2
 // c = r0 x r1 enters the products with the factor s / 32767 (s the folded
 // phase), i.e. U_2b = (s / 32767) conj(c_b).
+#include <stdlib.h>
+
 #include "stg_internal.h"
 
 #ifndef STG_FX2_MINBLOCKS
@@ -53,18 +55,41 @@ __device__ __forceinline__ void set2(Mat3x2 &u, int k, unsigned wa, unsigned wb)
     u.i[k / 3][k % 3] = unbias(fxb_hi(wa), fxb_hi(wb));
 }
 
-// link of site A (index sa) and site B (index sb) of one (parity, mu) block;
-// for 12-real, row 2 holds c = r0 x r1 (no conjugate, no sign, 32767^2 scale)
+// 12-real: row 2 is c = r0 x r1 (no conjugate, no sign, 32767^2 scale);
+// a / b hold rows 0-1 entries 0-3 of sites A / B, c / d entries 4-5
+__device__ __forceinline__ void decode12(const uint4 &a, const uint4 &b, const uint2 &c, const uint2 &d,
+                                         Mat3x2 &u)
+{
+    set2(u, 0, a.x, b.x);
+    set2(u, 1, a.y, b.y);
+    set2(u, 2, a.z, b.z);
+    set2(u, 3, a.w, b.w);
+    set2(u, 4, c.x, d.x);
+    set2(u, 5, c.y, d.y);
+#pragma unroll
+    for (int a2 = 0; a2 < 3; ++a2) {
+        const int b2 = (a2 + 1) % 3, c2 = (a2 + 2) % 3;
+        // c = r0_b r1_c - r0_c r1_b, split into positive and negative terms
+        const f2 pr = fma2(u.r[0][b2], u.r[1][c2], mul2(u.i[0][c2], u.i[1][b2]));
+        const f2 nr = fma2(u.i[0][b2], u.i[1][c2], mul2(u.r[0][c2], u.r[1][b2]));
+        const f2 pi = fma2(u.r[0][b2], u.i[1][c2], mul2(u.i[0][b2], u.r[1][c2]));
+        const f2 ni = fma2(u.r[0][c2], u.i[1][b2], mul2(u.i[0][c2], u.r[1][b2]));
+        u.r[2][a2] = sub2(pr, nr);
+        u.i[2][a2] = sub2(pi, ni);
+    }
+}
+
+// link of site A (index sa) and site B (index sb) of one (parity, mu) block
 template <int R>
 __device__ __forceinline__ void load_link2(const char *blk, int vh, int sa, int sb, Mat3x2 &u)
 {
     const uint4 *p = reinterpret_cast<const uint4 *>(blk);
     const uint4 a = ld_stream(p + sa), b = ld_stream(p + sb);
-    set2(u, 0, a.x, b.x);
-    set2(u, 1, a.y, b.y);
-    set2(u, 2, a.z, b.z);
-    set2(u, 3, a.w, b.w);
     if (R == 18) {
+        set2(u, 0, a.x, b.x);
+        set2(u, 1, a.y, b.y);
+        set2(u, 2, a.z, b.z);
+        set2(u, 3, a.w, b.w);
         const uint4 c = ld_stream(p + (size_t)vh + sa), d = ld_stream(p + (size_t)vh + sb);
         set2(u, 4, c.x, d.x);
         set2(u, 5, c.y, d.y);
@@ -74,20 +99,7 @@ __device__ __forceinline__ void load_link2(const char *blk, int vh, int sa, int 
         set2(u, 8, ld_stream(q + sa), ld_stream(q + sb));
     } else {
         const uint2 *q = reinterpret_cast<const uint2 *>(p + (size_t)vh);
-        const uint2 c = ld_stream(q + sa), d = ld_stream(q + sb);
-        set2(u, 4, c.x, d.x);
-        set2(u, 5, c.y, d.y);
-#pragma unroll
-        for (int a2 = 0; a2 < 3; ++a2) {
-            const int b2 = (a2 + 1) % 3, c2 = (a2 + 2) % 3;
-            // c = r0_b r1_c - r0_c r1_b, split into positive and negative terms
-            const f2 pr = fma2(u.r[0][b2], u.r[1][c2], mul2(u.i[0][c2], u.i[1][b2]));
-            const f2 nr = fma2(u.i[0][b2], u.i[1][c2], mul2(u.r[0][c2], u.r[1][b2]));
-            const f2 pi = fma2(u.r[0][b2], u.i[1][c2], mul2(u.i[0][b2], u.r[1][c2]));
-            const f2 ni = fma2(u.r[0][c2], u.i[1][b2], mul2(u.i[0][c2], u.r[1][b2]));
-            u.r[2][a2] = sub2(pr, nr);
-            u.i[2][a2] = sub2(pi, ni);
-        }
+        decode12(a, b, ld_stream(q + sa), ld_stream(q + sb), u);
     }
 }
 
@@ -219,6 +231,8 @@ __device__ __forceinline__ float epilogue(const DslashArgs &a, int vh, int i, co
 template <int R, int EPI>
 __global__ void __launch_bounds__(kBlock, STG_FX2_MINBLOCKS) k_dslash_fx2(const DslashArgs a)
 {
+    pdl_wait();
+    pdl_trigger();
     if (EPI == EPI_A_CG || EPI == EPI_GATE) {
         if (a.state->flag != FLAG_RUN) return;  // uniform over the grid
     }
@@ -297,24 +311,295 @@ __global__ void __launch_bounds__(kBlock, STG_FX2_MINBLOCKS) k_dslash_fx2(const 
     }
 }
 
-template <int R>
-static void launch_r(int epi, const DslashArgs &a, int grid, cudaStream_t s)
+// ---------------------------------------------------------------------------
+// Staged variant (12-real links from the tile-major copy).  The eight links
+// of an output site sit at that site's slot, so the links of one tile of
+// kFxTile output sites and one direction mu are a single contiguous block of
+// 48 KB.  One CTA of 16 warps per SM keeps a ring of four shared-memory
+// stages, one per mu, filled by bulk async copies (cp.async.bulk) whose
+// arrival an mbarrier counts in bytes; the threads compute two sites each
+// exactly as k_dslash_fx2 does, reading the links from shared memory.  The
+// warp that finishes reading stage mu last (a shared-memory arrival count)
+// refills it with the CTA's next tile, so there is no producer warp and the
+// 16 warps keep 128 registers each.  Up to three 48 KB stages per SM are in
+// flight, independent of the registers that capped the loads in flight of
+// the register-fed kernel.
+//
+// Each wait on an mbarrier gives up after about a second: it counts the
+// event in g_fx_wait_timeouts, the CG state gets FLAG_TIMEOUT (directly, or
+// through a NaN grid sum), and the CTA lets its own copies land before it
+// exits.
+// ---------------------------------------------------------------------------
+constexpr int kFxCons = kFxTile / 2;       // threads, two sites each
+constexpr int kFxConsWarps = kFxCons / 32;
+constexpr int kFxCtasPerSM = 1024 / kFxTile;  // 16 warps of 128 registers per SM
+constexpr unsigned kFxSmem = 4 * kFxStageBytes;
+constexpr unsigned long long kFxWaitNs = 1000000000ull;
+
+__device__ unsigned g_fx_wait_timeouts;
+
+__device__ __forceinline__ unsigned smem_addr(const void *p)
 {
-    switch (epi) {
-    case EPI_NONE: k_dslash_fx2<R, EPI_NONE><<<grid, kBlock, 0, s>>>(a); break;
-    case EPI_A: k_dslash_fx2<R, EPI_A><<<grid, kBlock, 0, s>>>(a); break;
-    case EPI_A_DOT: k_dslash_fx2<R, EPI_A_DOT><<<grid, kBlock, 0, s>>>(a); break;
-    case EPI_A_CG: k_dslash_fx2<R, EPI_A_CG><<<grid, kBlock, 0, s>>>(a); break;
-    case EPI_RES: k_dslash_fx2<R, EPI_RES><<<grid, kBlock, 0, s>>>(a); break;
-    case EPI_GATE: k_dslash_fx2<R, EPI_GATE><<<grid, kBlock, 0, s>>>(a); break;
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ bool mbar_try(unsigned bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile("{\n\t.reg .pred p;\n\t"
+                 "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+    return ok != 0u;
+}
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for the phase of the given parity to complete.  Gives up when
+// another thread of the CTA has given up (`abort`, unless null) or after
+// kFxWaitNs; the first to give up raises `abort` and counts the event.
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity, volatile int *abort)
+{
+    if (mbar_try(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (;;) {
+        if (mbar_try(bar, parity)) return true;
+        if (abort && *abort) return false;
+        if (global_ns() - t0 > kFxWaitNs) {
+            if (abort) *abort = 1;
+            atomicAdd(&g_fx_wait_timeouts, 1u);
+            return false;
+        }
     }
 }
 
-void launch_dslash_fx2(int recon, int epi, const DslashArgs &a, cudaStream_t s)
+// fill stage mu with the links of (tile, mu); one thread
+__device__ __forceinline__ void fill_stage(const char *lt, char *stage, unsigned long long *full, int tile,
+                                           int mu)
 {
+    const unsigned fb = smem_addr(&full[mu]);
+    const char *src = lt + ((size_t)tile * 4 + mu) * kFxStageBytes;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(fb), "r"(kFxStageBytes)
+                 : "memory");
+    // links are read once per half-pass: evict them from L2 first, so that
+    // the fields the CG kernels re-read stay resident
+    unsigned long long pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint "
+                 "[%0], [%1], %2, [%3], %4;"
+                 :: "r"(smem_addr(stage + (size_t)mu * kFxStageBytes)), "l"(src), "r"(kFxStageBytes), "r"(fb),
+                    "l"(pol)
+                 : "memory");
+}
+
+template <int EPI>
+__global__ void __launch_bounds__(kFxCons, kFxCtasPerSM) k_dslash_fx2_staged(const DslashArgs a)
+{
+    extern __shared__ __align__(128) char stage[];
+    __shared__ __align__(8) unsigned long long full[4];
+    __shared__ unsigned done_warps[4], issued[4];
+    __shared__ int abort_flag;
+    const int vh = a.g.Vh;
+    const int ntiles = (vh + kFxTile - 1) / kFxTile;
+    const int c = threadIdx.x, lane = c & 31;
+    if (c == 0) {
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_addr(&full[mu])) : "memory");
+            done_warps[mu] = 0u;
+            issued[mu] = 1u;
+        }
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) fill_stage(a.lt, stage, full, blockIdx.x, mu);
+    }
+    __syncthreads();
+    // the links are constant: the first fills may overlap the previous kernel
+    pdl_wait();
+    pdl_trigger();
+    if (EPI == EPI_A_CG || EPI == EPI_GATE) {
+        if (a.state->flag != FLAG_RUN) {  // uniform over the grid
+            if (c == 0) {
+#pragma unroll
+                for (int mu = 0; mu < 4; ++mu) mbar_wait(smem_addr(&full[mu]), 0u, nullptr);
+            }
+            return;
+        }
+    }
+    volatile int *abort = &abort_flag;
+    FF dot = {0.f, 0.f};
+    int j = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++j) {
+        const int iA = tile * kFxTile + c, iB = iA + kFxCons;
+        const bool okA = iA < vh, okB = iB < vh;
+        // slots past Vh compute on a valid site's fields (zero links), unstored
+        const int jA = okA ? iA : vh - 1, jB = okB ? iB : vh - 1;
+        uint4 wA = make_uint4(0u, 0u, 0u, 0u), wB = wA;
+        if (EPI == EPI_A || EPI == EPI_A_DOT || EPI == EPI_A_CG) {
+            wA = __ldg(static_cast<const uint4 *>(a.w) + jA);
+            wB = __ldg(static_cast<const uint4 *>(a.w) + jB);
+        }
+        const Site sA = site_of(a.g, jA, a.parity);
+        const Site sB = site_of(a.g, jB, a.parity);
+        Acc2 A;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) A.pr[k] = A.nr[k] = A.pi[k] = A.ni[k] = make_float2(0.f, 0.f);
+        bool alive = true;
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) {
+            int jfA, jbA, jfB, jbB;
+            neighbours(a.g, sA, jA, mu, jfA, jbA);
+            neighbours(a.g, sB, jB, mu, jfB, jbB);
+            float sfA, sbA, sfB, sbB;
+            link_signs(a.g, sA, mu, sfA, sbA);
+            link_signs(a.g, sB, mu, sfB, sbB);
+            const float k = LinkPost<PX16>::row2;
+            const f2 s2f = make_float2(sfA * k, sfB * k);
+            const f2 s2b = make_float2(sbA * k, sbB * k);
+            Vec3x2 vf, vb;
+            load_field2(a.in, jfA, jfB, vf);
+            load_field2(a.in, jbA, jbB, vb);
+            const bool ready = mbar_wait(smem_addr(&full[mu]), j & 1, abort);
+            if (!__all_sync(0xffffffffu, ready)) {
+                alive = false;
+                break;
+            }
+            const char *st = stage + (size_t)mu * kFxStageBytes;
+            const uint4 *f16 = reinterpret_cast<const uint4 *>(st);
+            const uint2 *f8 = reinterpret_cast<const uint2 *>(st + 16 * kFxTile);
+            const uint4 *b16 = reinterpret_cast<const uint4 *>(st + 24 * kFxTile);
+            const uint2 *b8 = reinterpret_cast<const uint2 *>(st + 40 * kFxTile);
+            const uint4 fa = f16[c], fb = f16[c + kFxCons];
+            const uint2 fc = f8[c], fd = f8[c + kFxCons];
+            const uint4 ba = b16[c], bb = b16[c + kFxCons];
+            const uint2 bc = b8[c], bd = b8[c + kFxCons];
+            // release the stage: the last warp to finish reading it refills
+            // it with this CTA's next tile
+            __syncwarp();
+            if (lane == 0) {
+                __threadfence_block();
+                if (atomicAdd(&done_warps[mu], 1u) == kFxConsWarps - 1) {
+                    done_warps[mu] = 0u;
+                    if (tile + (int)gridDim.x < ntiles) {
+                        __threadfence_block();
+                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                        fill_stage(a.lt, stage, full, tile + gridDim.x, mu);
+                        issued[mu] += 1u;
+                    }
+                }
+            }
+            Mat3x2 u;
+            decode12(fa, fb, fc, fd, u);
+            fwd2<12>(u, vf, s2f, A);
+            decode12(ba, bb, bc, bd, u);
+            bwd2<12>(u, vb, s2b, A);
+        }
+        if (!alive) {
+            dot.hi = __int_as_float(0x7fc00000);  // the grid sum becomes NaN
+            break;
+        }
+        const f2 kk = make_float2(LinkPost<PX16>::k, LinkPost<PX16>::k);
+        Vec3<float> accA, accB;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const f2 re = mul2(sub2(A.pr[q], A.nr[q]), kk);
+            const f2 im = mul2(sub2(A.pi[q], A.ni[q]), kk);
+            accA.r[q] = re.x;
+            accA.i[q] = im.x;
+            accB.r[q] = re.y;
+            accB.i[q] = im.y;
+        }
+        const float m2 = (EPI == EPI_A_CG) ? float(a.state->m2) : float(a.m2);
+        float dA = 0.f, dB = 0.f;
+        if (okA) dA = epilogue<EPI>(a, vh, iA, accA, m2, wA);
+        if (okB) dB = epilogue<EPI>(a, vh, iB, accB, m2, wB);
+        dot = ff_add(dot, FF{dA, 0.f});
+        dot = ff_add(dot, FF{dB, 0.f});
+    }
+    __syncthreads();
+    if (c == 0 && abort_flag) {
+        // after a timeout, let every copy issued into this CTA land first
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) mbar_wait(smem_addr(&full[mu]), (issued[mu] - 1u) & 1u, nullptr);
+        if (EPI == EPI_GATE) a.state->flag = FLAG_TIMEOUT;  // no grid sum here
+    }
+    if (EPI == EPI_A_DOT || EPI == EPI_A_CG || EPI == EPI_RES) {
+        double total;
+        if (grid_sum_ff<kFxCons>(dot, reinterpret_cast<float2 *>(a.partials), a.counter, total)) {
+            if (EPI == EPI_A_CG) {
+                CGState *st = a.state;
+                st->pAp = total;
+                if (!isfinite(total) && *(volatile unsigned *)&g_fx_wait_timeouts) st->flag = FLAG_TIMEOUT;
+                else if (!(total > 0.0) || !isfinite(total)) st->flag = FLAG_BREAKDOWN;
+                else st->alpha = st->delta_new / total;
+            } else {
+                *a.dot = total;
+            }
+        }
+    }
+}
+
+template <int EPI>
+static void launch_staged(const DslashArgs &a, cudaStream_t s, bool pdl)
+{
+    static int sms = 0;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_dslash_fx2_staged<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kFxSmem);
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 148;
+        attr = true;
+    }
+    // STG_FX16_GRID caps the CTA count (more tiles per CTA; for tests)
+    int cap = sms * kFxCtasPerSM;
+    if (const char *v = getenv("STG_FX16_GRID")) {
+        const int n = atoi(v);
+        if (n > 0 && n < cap) cap = n;
+    }
+    const int ntiles = (a.g.Vh + kFxTile - 1) / kFxTile;
+    const int grid = ntiles < cap ? ntiles : cap;
+    launch_k(k_dslash_fx2_staged<EPI>, grid, kFxCons, kFxSmem, s, pdl, a);
+}
+
+template <int R>
+static void launch_r(int epi, const DslashArgs &a, int grid, cudaStream_t s, bool pdl)
+{
+    switch (epi) {
+    case EPI_NONE: launch_k(k_dslash_fx2<R, EPI_NONE>, grid, kBlock, 0, s, pdl, a); break;
+    case EPI_A: launch_k(k_dslash_fx2<R, EPI_A>, grid, kBlock, 0, s, pdl, a); break;
+    case EPI_A_DOT: launch_k(k_dslash_fx2<R, EPI_A_DOT>, grid, kBlock, 0, s, pdl, a); break;
+    case EPI_A_CG: launch_k(k_dslash_fx2<R, EPI_A_CG>, grid, kBlock, 0, s, pdl, a); break;
+    case EPI_RES: launch_k(k_dslash_fx2<R, EPI_RES>, grid, kBlock, 0, s, pdl, a); break;
+    case EPI_GATE: launch_k(k_dslash_fx2<R, EPI_GATE>, grid, kBlock, 0, s, pdl, a); break;
+    }
+}
+
+void launch_dslash_fx2(int recon, int epi, const DslashArgs &a, cudaStream_t s, bool pdl)
+{
+    if (recon == 12 && a.lt) {
+        switch (epi) {
+        case EPI_NONE: launch_staged<EPI_NONE>(a, s, pdl); break;
+        case EPI_A: launch_staged<EPI_A>(a, s, pdl); break;
+        case EPI_A_DOT: launch_staged<EPI_A_DOT>(a, s, pdl); break;
+        case EPI_A_CG: launch_staged<EPI_A_CG>(a, s, pdl); break;
+        case EPI_RES: launch_staged<EPI_RES>(a, s, pdl); break;
+        case EPI_GATE: launch_staged<EPI_GATE>(a, s, pdl); break;
+        }
+        return;
+    }
     const int grid = (a.g.Vh + 2 * kBlock - 1) / (2 * kBlock);
-    if (recon == 18) launch_r<18>(epi, a, grid, s);
-    else launch_r<12>(epi, a, grid, s);
+    if (recon == 18) launch_r<18>(epi, a, grid, s, pdl);
+    else launch_r<12>(epi, a, grid, s, pdl);
 }
 
 }  // namespace stg

@@ -148,6 +148,66 @@ static stg_status pack_links(const Geom &g, const double2 *ucan, int prec, int r
     return STG_OK;
 }
 
+// Tile-major copy of FX16 / 12-real links (see kFxTile): one thread per
+// (output parity, tile, mu, slot).  The forward record is the link block
+// (p, mu) at the output site, the backward record the block (1 - p, mu) at
+// the backward neighbour; both are copied bit for bit.
+__global__ void k_tile_links_fx12(Geom g, const char *base, size_t blk_bytes, char *tiled, int ntiles)
+{
+    const long n = 2L * ntiles * 4 * kFxTile;
+    const long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int a = (int)(k % kFxTile);
+    long r = k / kFxTile;
+    const int mu = (int)(r % 4);
+    r /= 4;
+    const int tile = (int)(r % ntiles);
+    const int p = (int)(r / ntiles);
+    const int i = tile * kFxTile + a;
+    uint4 f16 = make_uint4(0u, 0u, 0u, 0u), b16 = f16;
+    uint2 f8 = make_uint2(0u, 0u), b8 = f8;
+    if (i < g.Vh) {
+        const Site s = site_of(g, i, p);
+        int jf, jb;
+        neighbours(g, s, i, mu, jf, jb);
+        const char *bf = base + (size_t)(p * 4 + mu) * blk_bytes;
+        const char *bb = base + (size_t)((1 - p) * 4 + mu) * blk_bytes;
+        f16 = reinterpret_cast<const uint4 *>(bf)[i];
+        f8 = reinterpret_cast<const uint2 *>(bf + (size_t)g.Vh * 16)[i];
+        b16 = reinterpret_cast<const uint4 *>(bb)[jb];
+        b8 = reinterpret_cast<const uint2 *>(bb + (size_t)g.Vh * 16)[jb];
+    }
+    char *blk = tiled + (((size_t)p * ntiles + tile) * 4 + mu) * kFxStageBytes;
+    reinterpret_cast<uint4 *>(blk)[a] = f16;
+    reinterpret_cast<uint2 *>(blk + 16 * kFxTile)[a] = f8;
+    reinterpret_cast<uint4 *>(blk + 24 * kFxTile)[a] = b16;
+    reinterpret_cast<uint2 *>(blk + 40 * kFxTile)[a] = b8;
+}
+
+static stg_status tile_links(const Geom &g, LinkField *lf, cudaStream_t s)
+{
+    const int ntiles = (g.Vh + kFxTile - 1) / kFxTile;
+    lf->tiled_parity_bytes = (size_t)ntiles * 4 * kFxStageBytes;
+    cudaError_t e = cudaMalloc((void **)&lf->tiled, 2 * lf->tiled_parity_bytes);
+    if (e != cudaSuccess) {
+        lf->tiled = nullptr;
+        set_error("stg_gauge_create: device allocation of the tile-major links failed");
+        return e == cudaErrorMemoryAllocation ? STG_ERR_OOM : cuda_fail(e, "cudaMalloc");
+    }
+    const long n = 2L * ntiles * 4 * kFxTile;
+    k_tile_links_fx12<<<(int)((n + 255) / 256), 256, 0, s>>>(g, lf->base, lf->blk_bytes, lf->tiled, ntiles);
+    STG_CUDA(cudaGetLastError());
+    return STG_OK;
+}
+
+// The staged FX16 / 12-real Dslash is the default; STG_FX16_TILED=0 at gauge
+// creation keeps the register-fed kernel (no tile-major copy).
+static bool want_tiled()
+{
+    const char *v = getenv("STG_FX16_TILED");
+    return !(v && v[0] == '0');
+}
+
 // ---------------------------------------------------------------------------
 // field packing
 // ---------------------------------------------------------------------------
@@ -242,12 +302,14 @@ stg_status gauge_create(const int dims[4], const double *links_host, int sloppy,
     const int recon_hi = (sloppy == P64) ? recon : 18;
     if (st == STG_OK) st = pack_links(g->geom, ucan, P64, recon_hi, &g->hi, s);
     if (st == STG_OK && sloppy != P64) st = pack_links(g->geom, ucan, sloppy, recon, &g->lo, s);
+    if (st == STG_OK && sloppy == PX16 && recon == 12 && want_tiled()) st = tile_links(g->geom, &g->lo, s);
     e = cudaStreamSynchronize(s);
     if (st == STG_OK && e != cudaSuccess) st = cuda_fail(e, "cudaStreamSynchronize");
     cudaFree(ucan);
     if (st != STG_OK) {
         if (g->hi.base) cudaFree(g->hi.base);
         if (g->lo.base) cudaFree(g->lo.base);
+        if (g->lo.tiled) cudaFree(g->lo.tiled);
         delete g;
         return st;
     }
@@ -264,6 +326,7 @@ void gauge_destroy(stg_gauge *g)
     if (g->ws) workspace_free(g->ws);
     if (g->hi.base) cudaFree(g->hi.base);
     if (g->lo.base) cudaFree(g->lo.base);
+    if (g->lo.tiled) cudaFree(g->lo.tiled);
     if (cur >= 0 && cur != g->device) cudaSetDevice(cur);
     delete g;
 }

@@ -566,7 +566,16 @@ __device__ __forceinline__ void adj_mul_sub(const Mat3<T> &u, const Vec3<T> &v, 
 // that can be captured once in a CUDA graph.
 // ---------------------------------------------------------------------------
 enum CGFlag { FLAG_RUN = 0, FLAG_CONVERGED = 1, FLAG_UPDATE = 2, FLAG_BREAKDOWN = 3,
-              FLAG_MAXITER = 4 };
+              FLAG_MAXITER = 4, FLAG_TIMEOUT = 5 };
+
+// Programmatic dependent launch: pdl_wait() returns once the preceding
+// kernel of the stream has completed and its writes are visible (at once when
+// the kernel was launched without the attribute); pdl_trigger() lets the next
+// kernel be scheduled.  Every kernel calls pdl_trigger() only after its
+// pdl_wait(), so when a kernel starts, all kernels before its immediate
+// predecessor have completed.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 struct CGState {
     double delta_new;  // r^dag r (iterated residual of the current precision)

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <string>
+#include <utility>
 
 #include "stg.h"
 #include "stg_common.cuh"
@@ -12,12 +13,43 @@ namespace stg {
 
 constexpr int kBlock = 256;  // threads per block of every site-parallel kernel
 
+// Launch with programmatic dependent launch when `pdl`: the kernel may start
+// while its predecessor on the stream finishes; it must call pdl_wait()
+// before touching anything the predecessor writes (stg_common.cuh).
+template <typename... K, typename... A>
+static inline cudaError_t launch_k(void (*kernel)(K...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                                   bool pdl, A &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = pdl ? at : nullptr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
+}
+
 // Device copy of the links in one precision / reconstruction.
+// Tile-major copy of FX16 / 12-real links for the staged Dslash: for output
+// parity p, tile k of kFxTile consecutive output sites and direction mu, one
+// contiguous block of kFxStageBytes holds the forward links U_mu(x) (uint4
+// [kFxTile] then uint2 [kFxTile]) followed by the backward links U_mu(x - mu)
+// of the same output sites, each record at the output site's slot; slots past
+// Vh are zero.  Every link appears twice (once per parity of output site).
+constexpr int kFxTile = 1024;
+constexpr unsigned kFxStageBytes = kFxTile * 48u;
+
 struct LinkField {
     char *base = nullptr;   // 8 blocks: (parity, mu) -> base + (2 * 4 ... ) see blk()
     int prec = -1;
     int recon = 18;
     size_t blk_bytes = 0;   // bytes of one (parity, mu) block, 256-aligned
+    char *tiled = nullptr;  // FX16 / 12-real only: tile-major copy (kFxTile)
+    size_t tiled_parity_bytes = 0;
     const char *blk(int parity, int mu) const { return base + (size_t)(parity * 4 + mu) * blk_bytes; }
 };
 
@@ -117,6 +149,7 @@ struct DslashLaunch {
     CGState *state;  // EPI_A_CG, EPI_GATE
     double *partials;
     unsigned *counter;
+    bool pdl;        // programmatic dependent launch (inside the CG graph)
 };
 
 stg_status launch_dslash(const Geom &g, int prec, int epi, const DslashLaunch &a, cudaStream_t s);
@@ -126,6 +159,7 @@ struct DslashArgs {
     Geom g;
     const char *lf[4];  // forward link blocks  (parity p,   mu)
     const char *lb[4];  // backward link blocks (parity 1-p, mu)
+    const char *lt;     // tile-major links of output parity p (FX16 / 12), or null
     int parity;
     const void *in;
     void *out;
@@ -139,7 +173,7 @@ struct DslashArgs {
 };
 
 // FX16 Dslash, two sites per thread on packed FP32x2 arithmetic
-void launch_dslash_fx2(int recon, int epi, const DslashArgs &a, cudaStream_t s);
+void launch_dslash_fx2(int recon, int epi, const DslashArgs &a, cudaStream_t s, bool pdl);
 
 int grid_for(long n);
 
