@@ -97,10 +97,11 @@ typedef struct stg_cg_params {
     long maxiter;      /* bound on the total iteration count (0 = 10 N_dim,
                           N_dim = 3 Vh as in Fig. 1)                           */
     int check_every;   /* inner iterations between host checks (0 = auto)     */
-    int timing;        /* 1: alternate chunks time the four kernels of their
-                          first iteration with CUDA events recorded inside the
-                          solver's graph, and the other chunks whole, with
-                          events around the graph launch (stats.t_*);
+    int timing;        /* 1: chunks rotate between timing the four kernels
+                          of their first iteration with CUDA events recorded
+                          inside the solver's graph, and timing whole chunks
+                          with events around the graph launch, with and
+                          without programmatic dependent launch (stats.t_*);
                           0: no events                                         */
 } stg_cg_params;
 
@@ -119,6 +120,10 @@ typedef struct stg_cg_stats {
     double t_xpay_ms;      /* mean duration: d = r + beta d                      */
     double t_iter_ms;      /* mean duration of one inner iteration, from events
                               around whole chunks without per-kernel events    */
+    double t_iter_serial_ms; /* the same for chunks launched without
+                              programmatic dependent launch (consecutive
+                              kernels do not overlap): the reference that
+                              calibrates the per-kernel event overhead        */
 } stg_cg_stats;
 
 typedef struct stg_gauge stg_gauge; /* opaque */

@@ -57,7 +57,7 @@ class stg_cg_stats(ctypes.Structure):
                 ("launches", ctypes.c_long), ("timed_iters", ctypes.c_long),
                 ("t_dslash_ms", ctypes.c_double), ("t_dslash_a_ms", ctypes.c_double),
                 ("t_update_ms", ctypes.c_double), ("t_xpay_ms", ctypes.c_double),
-                ("t_iter_ms", ctypes.c_double)]
+                ("t_iter_ms", ctypes.c_double), ("t_iter_serial_ms", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

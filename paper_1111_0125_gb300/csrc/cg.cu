@@ -335,8 +335,12 @@ static stg_status norm2(const Geom &g, int prec, const void *v, Workspace *ws, c
 
 // one CG iteration on the sloppy vectors (4 launches); with `ev`, CUDA
 // events are recorded before and after each kernel (5 events; external
-// records, so that stream capture turns them into event-record nodes)
-static stg_status iteration(stg_gauge *gg, Workspace *ws, int pd, cudaStream_t s, cudaEvent_t *ev)
+// records, so that stream capture turns them into event-record nodes); with
+// `pdl` (never together with events), consecutive kernels overlap by
+// programmatic dependent launch (each waits for its predecessor before
+// reading)
+static stg_status iteration(stg_gauge *gg, Workspace *ws, int pd, cudaStream_t s, cudaEvent_t *ev,
+                            bool pdl)
 {
     const Geom &g = gg->geom;
     const LinkField *lf = links_for(gg, pd);
@@ -346,9 +350,6 @@ static stg_status iteration(stg_gauge *gg, Workspace *ws, int pd, cudaStream_t s
     L.state = ws->state;
     L.partials = ws->partials;
     L.counter = &ws->state->counter;
-    // without per-kernel events, consecutive kernels overlap by programmatic
-    // dependent launch (each waits for its predecessor before reading)
-    const bool pdl = ev == nullptr;
     L.pdl = pdl;
     if (ev) STG_CUDA(cudaEventRecordWithFlags(ev[0], s, cudaEventRecordExternal));
     // the state flag gates every kernel, including the first half-pass
@@ -483,7 +484,7 @@ static stg_status prepare(stg_gauge *g, Workspace *ws, int pd)
         void *v[] = {ws->y, ws->r, ws->d, ws->q};
         for (void *p : v) cudaFree(p);
         ws->y = ws->r = ws->d = ws->q = nullptr;
-        for (int k = 0; k < 2; ++k)
+        for (int k = 0; k < 3; ++k)
             if (ws->graph[k]) {
                 cudaGraphExecDestroy(ws->graph[k]);
                 ws->graph[k] = nullptr;
@@ -506,10 +507,12 @@ static stg_status prepare(stg_gauge *g, Workspace *ws, int pd)
 
 // Capture `n` iterations as a graph on a private stream (capture is not
 // allowed on the legacy default stream), replayed on the caller's stream.
-// The timed variant records the 5 per-kernel events in its first iteration.
-static stg_status get_graph(stg_gauge *g, Workspace *ws, int pd, int n, int timed,
+// Variants: 0 plain, with programmatic dependent launch; 1 records the 5
+// per-kernel events in its first iteration; 2 plain without dependent launch.
+static stg_status get_graph(stg_gauge *g, Workspace *ws, int pd, int n, int variant,
                             cudaGraphExec_t *out)
 {
+    const int timed = variant;
     cudaGraphExec_t &ge = ws->graph[timed];
     if (ge && ws->graph_sloppy[timed] == pd && ws->graph_iters[timed] == n) {
         *out = ge;
@@ -519,7 +522,7 @@ static stg_status get_graph(stg_gauge *g, Workspace *ws, int pd, int n, int time
         cudaGraphExecDestroy(ge);
         ge = nullptr;
     }
-    if (timed && !ws->ev[0])
+    if (variant == 1 && !ws->ev[0])
         for (int k = 0; k < 5; ++k) STG_CUDA(cudaEventCreate(&ws->ev[k]));
     cudaStream_t cs;
     STG_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
@@ -528,7 +531,7 @@ static stg_status get_graph(stg_gauge *g, Workspace *ws, int pd, int n, int time
     stg_status st = STG_OK;
     if (e == cudaSuccess) {
         for (int k = 0; k < n && st == STG_OK; ++k)
-            st = iteration(g, ws, pd, cs, (timed && k == 0) ? ws->ev : nullptr);
+            st = iteration(g, ws, pd, cs, (variant == 1 && k == 0) ? ws->ev : nullptr, variant == 0);
         cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
         if (st == STG_OK && e2 != cudaSuccess) st = cuda_fail(e2, "cudaStreamEndCapture");
     } else {
@@ -606,8 +609,8 @@ stg_status cg_solve(stg_gauge *g, const double *src, double *x, double mass, dou
     if (chunk > 256) chunk = 256;
     long launches = 0;
     double tsum[4] = {0.0, 0.0, 0.0, 0.0};
-    double iter_sum = 0.0;
-    long iter_n = 0;
+    double iter_sum = 0.0, serial_sum = 0.0;
+    long iter_n = 0, serial_n = 0;
 
     // b, x0 into the FP64 device layout; |b|^2
     STG_TRY(pack_field(geo, P64, src, ws->b64, s));
@@ -659,9 +662,10 @@ stg_status cg_solve(stg_gauge *g, const double *src, double *x, double mass, dou
         h->track_max = (p->policy == STG_CG_RELIABLE) ? 1 : 0;
         h->counter = 0;
         if (status == STG_OK) status = write_state(ws, s);
-        cudaGraphExec_t graph = nullptr, graph_timed = nullptr;
+        cudaGraphExec_t graph = nullptr, graph_timed = nullptr, graph_serial = nullptr;
         if (status == STG_OK) status = get_graph(g, ws, pd, chunk, 0, &graph);
         if (status == STG_OK && p->timing) status = get_graph(g, ws, pd, chunk, 1, &graph_timed);
+        if (status == STG_OK && p->timing) status = get_graph(g, ws, pd, chunk, 2, &graph_serial);
         if (status == STG_OK && p->timing && !ws->ev_chunk[0]) {
             for (int k = 0; k < 2 && status == STG_OK; ++k) {
                 cudaError_t e = cudaEventCreate(&ws->ev_chunk[k]);
@@ -671,14 +675,18 @@ stg_status cg_solve(stg_gauge *g, const double *src, double *x, double mass, dou
         int breakdowns = 0;
         long chunk_no = 0;
         while (status == STG_OK) {
-            // with timing, chunks alternate: per-kernel events in even chunks,
-            // events around the whole launch of odd (plain) chunks
-            const bool kernel_timed = p->timing && (chunk_no % 2 == 0);
+            // with timing, chunks rotate: per-kernel events; events around
+            // the whole launch of a plain chunk; the same without dependent
+            // launch (serial kernels)
+            const int phase = (int)(chunk_no % 3);
+            const bool kernel_timed = p->timing && phase == 0;
             const bool chunk_timed = p->timing && !kernel_timed;
+            const bool serial = p->timing && phase == 2;
             ++chunk_no;
             cudaError_t e = cudaSuccess;
             if (chunk_timed) e = cudaEventRecord(ws->ev_chunk[0], s);
-            if (e == cudaSuccess) e = cudaGraphLaunch(kernel_timed ? graph_timed : graph, s);
+            if (e == cudaSuccess)
+                e = cudaGraphLaunch(kernel_timed ? graph_timed : (serial ? graph_serial : graph), s);
             if (e == cudaSuccess && chunk_timed) e = cudaEventRecord(ws->ev_chunk[1], s);
             if (e != cudaSuccess) {
                 status = cuda_fail(e, "cudaGraphLaunch");
@@ -691,8 +699,13 @@ stg_status cg_solve(stg_gauge *g, const double *src, double *x, double mass, dou
                 // every iteration of the chunk ran in full
                 float ms = 0.f;
                 if (cudaEventElapsedTime(&ms, ws->ev_chunk[0], ws->ev_chunk[1]) == cudaSuccess) {
-                    iter_sum += ms / chunk;
-                    ++iter_n;
+                    if (serial) {
+                        serial_sum += ms / chunk;
+                        ++serial_n;
+                    } else {
+                        iter_sum += ms / chunk;
+                        ++iter_n;
+                    }
                 } else {
                     cudaGetLastError();
                 }
@@ -776,6 +789,7 @@ stg_status cg_solve(stg_gauge *g, const double *src, double *x, double mass, dou
         st.t_xpay_ms = tsum[3] / st.timed_iters;
     }
     if (iter_n > 0) st.t_iter_ms = iter_sum / iter_n;
+    if (serial_n > 0) st.t_iter_serial_ms = serial_sum / serial_n;
     // setup: 2 packs, norm, residual (2), reset; per update: accumulate,
     // residual (2), reset; final unpack
     launches += 6 + 4L * st.updates + 1;

@@ -382,7 +382,7 @@ void workspace_free(Workspace *ws)
     if (!ws) return;
     batch_destroy(ws->batch);
     cudaFree(ws->mrhs_tmp);
-    for (int k = 0; k < 2; ++k)
+    for (int k = 0; k < 3; ++k)
         if (ws->graph[k]) cudaGraphExecDestroy(ws->graph[k]);
     for (int k = 0; k < 5; ++k)
         if (ws->ev[k]) cudaEventDestroy(ws->ev[k]);

@@ -120,9 +120,10 @@ struct Workspace {
     void *x64 = nullptr, *b64 = nullptr, *r64 = nullptr, *t64 = nullptr;
     void *y = nullptr, *r = nullptr, *d = nullptr, *q = nullptr;
     int cg_sloppy = -1;
-    // captured chunks of iterations: [0] plain, [1] with per-kernel events
-    cudaGraphExec_t graph[2] = {nullptr, nullptr};
-    int graph_sloppy[2] = {-1, -1}, graph_iters[2] = {0, 0};
+    // captured chunks of iterations: [0] plain (programmatic dependent
+    // launch), [1] with per-kernel events, [2] plain without dependent launch
+    cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};
+    int graph_sloppy[3] = {-1, -1, -1}, graph_iters[3] = {0, 0, 0};
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // per-kernel events
     cudaEvent_t ev_chunk[2] = {nullptr, nullptr};                        // around plain chunks
     stg_batch *batch = nullptr;       // session cached for stg_cg_solve_mrhs
