@@ -321,7 +321,9 @@ def run_c4(args):
     s1.synchronize()
     t_m = s0.elapsed_time(s1) / 20
     L, S = LINK_BYTES[(args.sloppy, args.recon)], FIELD_BYTES[args.sloppy]
-    nbytes = vh * (8 * L * -(-n // (nb * tb)) + 2 * S * n)   # links once per NB x TPS systems
+    # links once per NB x TPS systems (register-fed), once for all (staged, tb = 0)
+    link_passes = 1 if tb == 0 else -(-n // (nb * tb))
+    nbytes = vh * (8 * L * link_passes + 2 * S * n)
     peak, src_ = measured_hbm()
     achieved = nbytes / (t_m / 1000.0) / 1e9
     print(json.dumps({
@@ -338,7 +340,9 @@ def run_c4(args):
         "iters": [s_["iters"] for s_ in st], "updates": [s_["updates"] for s_ in st],
         "true_res_max": max(s_["true_res"] for s_ in st),
         "iters_one_by_one": [s_["iters"] for s_ in single],
-        "mrhs_dslash": {"rhs_block": nb, "threads_per_site": tb, "launch_ms": t_m,
+        "mrhs_dslash": {"rhs_block": nb, "threads_per_site": tb,
+                        "kernel": "k_dslash_ms (staged)" if tb == 0 else "k_dslash_m",
+                        "launch_ms": t_m,
                         "algorithmic_bytes_per_launch": nbytes,
                         "bytes_per_site_per_system": nbytes / vh / n,
                         "achieved": achieved, "peak": peak, "peak_source": src_, "unit": "GB/s",

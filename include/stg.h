@@ -312,7 +312,11 @@ size_t stg_batch_bytes(const stg_gauge *g, int max_systems, stg_prec sloppy);
 
 /* The autotuner's choice (rhs_block = NB systems per thread and block,
  * threads_per_site = TPS) for this handle's lattice, `prec` and nrhs;
- * STG_ERR_INVALID_ARG if not tuned yet. */
+ * threads_per_site = 0 names the staged kernel (12-real FP32 / FX16 links
+ * streamed through shared memory, one link load per site for all systems,
+ * NB systems per thread and pass).  STG_ERR_INVALID_ARG if not tuned yet.
+ * The environment variable STG_MRHS_SHAPE=<k> forces shape k (0-8:
+ * register-fed (NB, TPS); 9-11: staged NB = 2, 4, 8) where it applies. */
 stg_status stg_mrhs_tuning(const stg_gauge *g, stg_prec prec, int nrhs, int *rhs_block,
                            int *threads_per_site);
 

@@ -342,67 +342,17 @@ constexpr int kFxCons = kFxTile / 2;       // threads, two sites each
 constexpr int kFxConsWarps = kFxCons / 32;
 constexpr int kFxCtasPerSM = 1024 / kFxTile;  // 16 warps of 128 registers per SM
 constexpr unsigned kFxSmem = 4 * kFxStageBytes;
-constexpr unsigned long long kFxWaitNs = 1000000000ull;
 
 __device__ unsigned g_fx_wait_timeouts;
 
-__device__ __forceinline__ unsigned smem_addr(const void *p)
-{
-    return (unsigned)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ bool mbar_try(unsigned bar, unsigned parity)
-{
-    unsigned ok;
-    asm volatile("{\n\t.reg .pred p;\n\t"
-                 "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-                 "selp.u32 %0, 1, 0, p;\n\t}"
-                 : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
-    return ok != 0u;
-}
-
-__device__ __forceinline__ unsigned long long global_ns()
-{
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Wait for the phase of the given parity to complete.  Gives up when
-// another thread of the CTA has given up (`abort`, unless null) or after
-// kFxWaitNs; the first to give up raises `abort` and counts the event.
-__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity, volatile int *abort)
-{
-    if (mbar_try(bar, parity)) return true;
-    const unsigned long long t0 = global_ns();
-    for (;;) {
-        if (mbar_try(bar, parity)) return true;
-        if (abort && *abort) return false;
-        if (global_ns() - t0 > kFxWaitNs) {
-            if (abort) *abort = 1;
-            atomicAdd(&g_fx_wait_timeouts, 1u);
-            return false;
-        }
-    }
-}
-
-// fill stage mu with the links of (tile, mu); one thread
+// fill stage mu with the links of (tile, mu); one thread.  Links are read
+// once per half-pass: L2 evicts them first, so the fields that the CG
+// kernels re-read stay resident.
 __device__ __forceinline__ void fill_stage(const char *lt, char *stage, unsigned long long *full, int tile,
                                            int mu)
 {
-    const unsigned fb = smem_addr(&full[mu]);
-    const char *src = lt + ((size_t)tile * 4 + mu) * kFxStageBytes;
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(fb), "r"(kFxStageBytes)
-                 : "memory");
-    // links are read once per half-pass: evict them from L2 first, so that
-    // the fields the CG kernels re-read stay resident
-    unsigned long long pol;
-    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint "
-                 "[%0], [%1], %2, [%3], %4;"
-                 :: "r"(smem_addr(stage + (size_t)mu * kFxStageBytes)), "l"(src), "r"(kFxStageBytes), "r"(fb),
-                    "l"(pol)
-                 : "memory");
+    bulk_load(stage + (size_t)mu * kFxStageBytes, lt + ((size_t)tile * 4 + mu) * kFxStageBytes, kFxStageBytes,
+              &full[mu]);
 }
 
 template <int EPI>
@@ -443,7 +393,7 @@ __global__ void __launch_bounds__(kFxCons, kFxCtasPerSM) k_dslash_fx2_staged(con
         if (a.state->flag != FLAG_RUN) {  // uniform over the grid
             if (c == 0 && prefetch) {
 #pragma unroll
-                for (int mu = 0; mu < 4; ++mu) mbar_wait(smem_addr(&full[mu]), 0u, nullptr);
+                for (int mu = 0; mu < 4; ++mu) mbar_wait(smem_addr(&full[mu]), 0u, nullptr, &g_fx_wait_timeouts);
             }
             return;
         }
@@ -487,7 +437,7 @@ __global__ void __launch_bounds__(kFxCons, kFxCtasPerSM) k_dslash_fx2_staged(con
             Vec3x2 vf, vb;
             load_field2(a.in, jfA, jfB, vf);
             load_field2(a.in, jbA, jbB, vb);
-            const bool ready = mbar_wait(smem_addr(&full[mu]), j & 1, abort);
+            const bool ready = mbar_wait(smem_addr(&full[mu]), j & 1, abort, &g_fx_wait_timeouts);
             if (!__all_sync(0xffffffffu, ready)) {
                 alive = false;
                 break;
@@ -548,7 +498,7 @@ __global__ void __launch_bounds__(kFxCons, kFxCtasPerSM) k_dslash_fx2_staged(con
     if (c == 0 && abort_flag) {
         // after a timeout, let every copy issued into this CTA land first
 #pragma unroll
-        for (int mu = 0; mu < 4; ++mu) mbar_wait(smem_addr(&full[mu]), (issued[mu] - 1u) & 1u, nullptr);
+        for (int mu = 0; mu < 4; ++mu) mbar_wait(smem_addr(&full[mu]), (issued[mu] - 1u) & 1u, nullptr, &g_fx_wait_timeouts);
         if (EPI == EPI_GATE) a.state->flag = FLAG_TIMEOUT;  // no grid sum here
     }
     if (EPI == EPI_A_DOT || EPI == EPI_A_CG || EPI == EPI_RES) {

@@ -200,6 +200,83 @@ static stg_status tile_links(const Geom &g, LinkField *lf, cudaStream_t s)
     return STG_OK;
 }
 
+// Tile-major copy for the staged multi-system Dslash (see kMTile): one
+// thread per (output parity, tile, mu, dir, slot); records copied bit for
+// bit from the link blocks (forward: block (p, mu) at the site; backward:
+// block (1 - p, mu) at the backward neighbour).
+template <int P>
+__global__ void k_mtile_links(Geom g, const char *base, size_t blk_bytes, char *mtiled, int ntiles)
+{
+    constexpr int L = P == P32 ? 48 : 24;
+    const long n = 2L * ntiles * 8 * kMTile;
+    const long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int a = (int)(k % kMTile);
+    long r = k / kMTile;
+    const int md = (int)(r % 8);  // mu * 2 + dir
+    r /= 8;
+    const int tile = (int)(r % ntiles);
+    const int p = (int)(r / ntiles);
+    const int mu = md >> 1, dir = md & 1;
+    const int i = tile * kMTile + a;
+    char *blk = mtiled + ((size_t)p * ntiles + tile) * ((size_t)kMTile * 8 * L) + (size_t)md * kMTile * L;
+    const int vh = g.Vh;
+    int src = i, sp = p;
+    const bool ok = i < vh;
+    if (ok && dir == 1) {
+        const Site s = site_of(g, i, p);
+        int jf, jb;
+        neighbours(g, s, i, mu, jf, jb);
+        src = jb;
+        sp = 1 - p;
+    }
+    const char *from = base + (size_t)(sp * 4 + mu) * blk_bytes;
+    if (P == P32) {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (ok) v = reinterpret_cast<const float4 *>(from)[(size_t)q * vh + src];
+            reinterpret_cast<float4 *>(blk)[q * kMTile + a] = v;
+        }
+    } else {
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        uint2 w = make_uint2(0u, 0u);
+        if (ok) {
+            v = reinterpret_cast<const uint4 *>(from)[src];
+            w = reinterpret_cast<const uint2 *>(from + (size_t)vh * 16)[src];
+        }
+        reinterpret_cast<uint4 *>(blk)[a] = v;
+        reinterpret_cast<uint2 *>(blk + 16 * kMTile)[a] = w;
+    }
+}
+
+static stg_status mtile_links(const Geom &g, LinkField *lf, cudaStream_t s)
+{
+    const int ntiles = (g.Vh + kMTile - 1) / kMTile;
+    lf->mtile_bytes = (size_t)kMTile * 8 * (lf->prec == P32 ? 48 : 24);
+    lf->mtiled_parity_bytes = (size_t)ntiles * lf->mtile_bytes;
+    cudaError_t e = cudaMalloc((void **)&lf->mtiled, 2 * lf->mtiled_parity_bytes);
+    if (e != cudaSuccess) {
+        lf->mtiled = nullptr;
+        set_error("stg_gauge_create: device allocation of the multi-system tile-major links failed");
+        return e == cudaErrorMemoryAllocation ? STG_ERR_OOM : cuda_fail(e, "cudaMalloc");
+    }
+    const long n = 2L * ntiles * 8 * kMTile;
+    const int grid = (int)((n + 255) / 256);
+    if (lf->prec == P32) k_mtile_links<P32><<<grid, 256, 0, s>>>(g, lf->base, lf->blk_bytes, lf->mtiled, ntiles);
+    else k_mtile_links<PX16><<<grid, 256, 0, s>>>(g, lf->base, lf->blk_bytes, lf->mtiled, ntiles);
+    STG_CUDA(cudaGetLastError());
+    return STG_OK;
+}
+
+// STG_MRHS_TILED=0 at gauge creation leaves out the multi-system copy (the
+// autotuner then only has the register-fed multi-system kernels).
+static bool want_mtiled()
+{
+    const char *v = getenv("STG_MRHS_TILED");
+    return !(v && v[0] == '0');
+}
+
 // The staged FX16 / 12-real Dslash is the default; STG_FX16_TILED=0 at gauge
 // creation keeps the register-fed kernel (no tile-major copy).
 static bool want_tiled()
@@ -303,6 +380,8 @@ stg_status gauge_create(const int dims[4], const double *links_host, int sloppy,
     if (st == STG_OK) st = pack_links(g->geom, ucan, P64, recon_hi, &g->hi, s);
     if (st == STG_OK && sloppy != P64) st = pack_links(g->geom, ucan, sloppy, recon, &g->lo, s);
     if (st == STG_OK && sloppy == PX16 && recon == 12 && want_tiled()) st = tile_links(g->geom, &g->lo, s);
+    if (st == STG_OK && (sloppy == P32 || sloppy == PX16) && recon == 12 && want_mtiled())
+        st = mtile_links(g->geom, &g->lo, s);
     e = cudaStreamSynchronize(s);
     if (st == STG_OK && e != cudaSuccess) st = cuda_fail(e, "cudaStreamSynchronize");
     cudaFree(ucan);
@@ -310,6 +389,7 @@ stg_status gauge_create(const int dims[4], const double *links_host, int sloppy,
         if (g->hi.base) cudaFree(g->hi.base);
         if (g->lo.base) cudaFree(g->lo.base);
         if (g->lo.tiled) cudaFree(g->lo.tiled);
+        if (g->lo.mtiled) cudaFree(g->lo.mtiled);
         delete g;
         return st;
     }
@@ -327,6 +407,7 @@ void gauge_destroy(stg_gauge *g)
     if (g->hi.base) cudaFree(g->hi.base);
     if (g->lo.base) cudaFree(g->lo.base);
     if (g->lo.tiled) cudaFree(g->lo.tiled);
+    if (g->lo.mtiled) cudaFree(g->lo.mtiled);
     if (cur >= 0 && cur != g->device) cudaSetDevice(cur);
     delete g;
 }

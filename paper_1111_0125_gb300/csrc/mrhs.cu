@@ -49,7 +49,14 @@ static bool same_key(const TuneEntry &e, const int *dims, int prec, int recon, i
            e.dims[3] == dims[3] && e.prec == prec && e.recon == recon && e.nrhs == nrhs;
 }
 
-static bool valid_choice(int shape) { return shape >= 0 && shape < kMrhsShapes; }
+// shapes 0 .. kMrhsShapes - 1: register-fed (NB, TPS); then the staged
+// kernel with NB = ms_nb(shape - kMrhsShapes) (12-real FP32 / FX16 links)
+static bool valid_choice(int shape) { return shape >= 0 && shape < kMrhsShapes + kMrhsStagedShapes; }
+
+static bool staged_ok(const LinkField *lf)
+{
+    return lf->mtiled && lf->recon == 12 && (lf->prec == P32 || lf->prec == PX16);
+}
 
 static void tune_load_file_locked()
 {
@@ -117,6 +124,14 @@ static stg_status launch_m(const stg_gauge *g, const LinkField *lf, int shape, i
         a.lf[mu] = lf->blk(a.parity, mu);
         a.lb[mu] = lf->blk(1 - a.parity, mu);
     }
+    a.lt = nullptr;
+    if (shape >= kMrhsShapes) {
+        if (!staged_ok(lf)) {
+            set_error("multi-system Dslash: the staged kernel needs the tile-major 12-real links");
+            return STG_ERR_UNSUPPORTED;
+        }
+        a.lt = lf->mtiled + (size_t)a.parity * lf->mtiled_parity_bytes;
+    }
     if (lf->prec == P32 && lf->recon == 12) launch_dslash_m_f32_12(shape, epi, a, s);
     else if (lf->prec == P32) launch_dslash_m_f32_18(shape, epi, a, s);
     else if (lf->prec == PX16 && lf->recon == 12) launch_dslash_m_fx16_12(shape, epi, a, s);
@@ -129,13 +144,28 @@ static stg_status launch_m(const stg_gauge *g, const LinkField *lf, int shape, i
     return STG_OK;
 }
 
-// Time one EPI_NONE half-pass of all n systems for every (NB, threads per
-// site) shape with TPS <= n (one warm-up and three timed launches each, CUDA
-// events on `s`) and keep the fastest.  `out` (n fields) is overwritten.
+// STG_MRHS_SHAPE=<k> forces shape k where it applies (tests, benchmarks)
+static bool forced_shape(const LinkField *lf, int n, int *shape)
+{
+    const char *v = getenv("STG_MRHS_SHAPE");
+    if (!v) return false;
+    const int k = atoi(v);
+    if (!valid_choice(k) || !(k < kMrhsShapes ? mrhs_tps(k) <= n : staged_ok(lf))) return false;
+    *shape = k;
+    return true;
+}
+
+// Time one EPI_NONE half-pass of all n systems for every register-fed (NB,
+// threads per site) shape with TPS <= n and every staged NB (one warm-up and
+// three timed launches each, CUDA events on `s`) and keep the fastest.
+// `out` (n fields) is overwritten.
 static stg_status tune(const stg_gauge *g, const LinkField *lf, int n, const void *in, void *out,
                        size_t fstride, cudaStream_t s, int *shape_out)
 {
-    if (tune_lookup(g->dims, lf->prec, lf->recon, n, shape_out)) return STG_OK;
+    if (forced_shape(lf, n, shape_out)) return STG_OK;
+    if (tune_lookup(g->dims, lf->prec, lf->recon, n, shape_out) &&
+        (*shape_out < kMrhsShapes || staged_ok(lf)))
+        return STG_OK;
     cudaEvent_t e0, e1;
     STG_CUDA(cudaEventCreate(&e0));
     cudaError_t ce = cudaEventCreate(&e1);
@@ -146,8 +176,15 @@ static stg_status tune(const stg_gauge *g, const LinkField *lf, int n, const voi
     float best = 1e30f;
     int bshape = 0;
     stg_status st = STG_OK;
-    for (int k = 0; k < kMrhsShapes && st == STG_OK; ++k) {
-        if (mrhs_tps(k) > n || (mrhs_tps(k) == 1 && mrhs_nb(k) > n && mrhs_nb(k) > 1)) continue;
+    for (int k = 0; k < kMrhsShapes + kMrhsStagedShapes && st == STG_OK; ++k) {
+        if (k < kMrhsShapes) {
+            if (mrhs_tps(k) > n || (mrhs_tps(k) == 1 && mrhs_nb(k) > n && mrhs_nb(k) > 1)) continue;
+        } else {
+            // the site groups of a staged CTA share the systems: a block
+            // larger than a group's share only adds idle slots
+            const int nb = ms_nb(k - kMrhsShapes);
+            if (!staged_ok(lf) || (nb > 2 && nb > (n + kMsGroups - 1) / kMsGroups)) continue;
+        }
         MrhsArgs a = {};
         a.parity = 1;
         a.in = static_cast<const char *>(in);
@@ -858,12 +895,17 @@ stg_status stg_mrhs_tuning(const stg_gauge *g, stg_prec prec, int nrhs, int *rhs
         return STG_ERR_INVALID_ARG;
     }
     int shape;
-    if (!tune_lookup(g->dims, lf->prec, lf->recon, nrhs, &shape)) {
+    if (!forced_shape(lf, nrhs, &shape) && !tune_lookup(g->dims, lf->prec, lf->recon, nrhs, &shape)) {
         set_error("stg_mrhs_tuning: not tuned yet for this lattice, precision and nrhs");
         return STG_ERR_INVALID_ARG;
     }
-    *rhs_block = mrhs_nb(shape);
-    *threads_per_site = mrhs_tps(shape);
+    if (shape >= kMrhsShapes) {
+        *rhs_block = ms_nb(shape - kMrhsShapes);
+        *threads_per_site = 0;  // staged: one link load per site serves all systems
+    } else {
+        *rhs_block = mrhs_nb(shape);
+        *threads_per_site = mrhs_tps(shape);
+    }
     return STG_OK;
 }
 

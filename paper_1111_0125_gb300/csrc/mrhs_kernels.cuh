@@ -17,6 +17,8 @@
 // systems in a fixed order).
 #pragma once
 
+#include <stdlib.h>
+
 #include "stg_internal.h"
 
 namespace stg {
@@ -40,6 +42,7 @@ struct MrhsArgs {
     float2 *partials;      // EPI_A_CG: [nrhs][gridDim.x]
     unsigned *counter;     // EPI_A_CG: arrival counter
     int grid_cap;          // blocks launched at most (they stride over site tiles)
+    const char *lt;        // staged kernel: tile-major links of the output parity
 };
 
 constexpr int kMrhsBlock = 256;
@@ -232,6 +235,428 @@ __global__ void __launch_bounds__(kMrhsBlock) k_dslash_m(const MrhsArgs a)
         __syncthreads();
         if (threadIdx.x == 0) *a.counter = 0u;
     }
+}
+
+// ---------------------------------------------------------------------------
+// Staged multi-system Dslash, 12-real FP32 or FX16 links from the tile-major
+// copy (kMTile).  A CTA of 256 threads (two per SM) walks tiles of kMTile =
+// 64 output sites; the tile's eight links (24 KB in FP32) arrive in shared
+// memory by one bulk async copy into a ring of two stages and serve every
+// system, so the links cost 8L / n per site and system for n systems
+// instead of 8L / NB.  Thread t owns site t % 64 of the tile and, with the
+// other threads of its group (t / 64, four groups), a quarter of the active
+// systems, NB at a time in registers; the link is rebuilt once per NB
+// systems (FX16: applied to two systems per FP32x2 instruction).
+//
+// Each warp adds its part of d_k^dag q_k into its own shared-memory slots,
+// summed in a fixed order at the end (no barrier inside the system loop).
+// The last warp to finish a tile refills that stage with the CTA's tile
+// two steps ahead.  Waits on the stage barriers give up after about a
+// second (g_ms_wait_timeouts; the CTA then lets its copies land), and the
+// systems' reductions become NaN, which stops them.
+// ---------------------------------------------------------------------------
+#ifndef STG_MS_THREADS
+#define STG_MS_THREADS 256
+#endif
+#ifndef STG_MS_STAGES
+#define STG_MS_STAGES 2
+#endif
+#ifndef STG_MS_MINBLOCKS
+#define STG_MS_MINBLOCKS 2
+#endif
+constexpr int kMsThreads = STG_MS_THREADS;
+constexpr int kMsGroups = kMsThreads / kMTile;
+constexpr int kMsWarps = kMsThreads / 32;
+constexpr int kMsStages = STG_MS_STAGES;
+
+static __device__ unsigned g_ms_wait_timeouts;
+
+template <int P> struct MsLink;
+template <> struct MsLink<P32> {
+    static constexpr unsigned kRec = 48;
+    __device__ __forceinline__ static Mat3<float> load(const char *blk, int a, float s2)
+    {
+        const float4 *p = reinterpret_cast<const float4 *>(blk);
+        Mat3<float> u;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float4 v = p[k * kMTile + a];
+            set_entry(u, 2 * k, v.x, v.y);
+            set_entry(u, 2 * k + 1, v.z, v.w);
+        }
+        reconstruct_row2(u, s2);
+        return u;
+    }
+};
+template <> struct MsLink<PX16> {
+    static constexpr unsigned kRec = 24;
+    __device__ __forceinline__ static Mat3<float> load(const char *blk, int a, float s2)
+    {
+        const uint4 v = reinterpret_cast<const uint4 *>(blk)[a];
+        const uint2 w = reinterpret_cast<const uint2 *>(blk + 16 * kMTile)[a];
+        Mat3<float> u;
+        set_entry(u, 0, fx_lo(v.x), fx_hi(v.x));
+        set_entry(u, 1, fx_lo(v.y), fx_hi(v.y));
+        set_entry(u, 2, fx_lo(v.z), fx_hi(v.z));
+        set_entry(u, 3, fx_lo(v.w), fx_hi(v.w));
+        set_entry(u, 4, fx_lo(w.x), fx_hi(w.x));
+        set_entry(u, 5, fx_lo(w.y), fx_hi(w.y));
+        reconstruct_row2(u, s2);
+        return u;
+    }
+};
+
+// Two systems in the halves of every float2 (one sm_100 FP32x2 instruction
+// for both): acc += U v and acc -= U^dag v with U shared (row 2 already
+// carrying its sign); the negated link entries cost no instruction.
+__device__ __forceinline__ float2 bc2(float x) { return make_float2(x, x); }
+
+__device__ __forceinline__ void mul_add2(const Mat3<float> &u, const float2 *vr, const float2 *vi,
+                                         float2 *ar, float2 *ai)
+{
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            ar[a] = __ffma2_rn(bc2(u.r[a][b]), vr[b], ar[a]);
+            ar[a] = __ffma2_rn(bc2(-u.i[a][b]), vi[b], ar[a]);
+            ai[a] = __ffma2_rn(bc2(u.r[a][b]), vi[b], ai[a]);
+            ai[a] = __ffma2_rn(bc2(u.i[a][b]), vr[b], ai[a]);
+        }
+}
+
+__device__ __forceinline__ void adj_mul_sub2(const Mat3<float> &u, const float2 *vr, const float2 *vi,
+                                             float2 *ar, float2 *ai)
+{
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            // conj(U_ba) v_b = (u.r v.r + u.i v.i) + i (u.r v.i - u.i v.r)
+            ar[a] = __ffma2_rn(bc2(-u.r[b][a]), vr[b], ar[a]);
+            ar[a] = __ffma2_rn(bc2(-u.i[b][a]), vi[b], ar[a]);
+            ai[a] = __ffma2_rn(bc2(-u.r[b][a]), vi[b], ai[a]);
+            ai[a] = __ffma2_rn(bc2(u.i[b][a]), vr[b], ai[a]);
+        }
+}
+
+template <int P>
+__host__ __device__ constexpr unsigned ms_stage_bytes() { return kMTile * 8 * MsLink<P>::kRec; }
+
+template <int P, int NB, int EPI>
+__global__ void __launch_bounds__(kMsThreads, STG_MS_MINBLOCKS) k_dslash_ms(const MrhsArgs a)
+{
+    typedef float T;
+    constexpr unsigned SB = ms_stage_bytes<P>();
+    constexpr unsigned LB = kMTile * MsLink<P>::kRec;  // one (mu, dir) block
+    extern __shared__ __align__(128) char stage[];
+    __shared__ __align__(8) unsigned long long full[kMsStages];
+    __shared__ unsigned done_warps[kMsStages], issued[kMsStages];
+    __shared__ int abort_flag;
+    __shared__ FF sysw[kMsWarps][kMaxRhs];  // EPI_A_CG: per-warp d^dag q per list slot
+    const int vh = a.g.Vh;
+    const int ntiles = (vh + kMTile - 1) / kMTile;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int site = threadIdx.x % kMTile, grp = threadIdx.x / kMTile;
+    const int nact = a.active ? *a.nactive : a.nrhs;
+    const int per = (nact + kMsGroups - 1) / kMsGroups;  // list slots per group (uniform bound)
+
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < kMsStages; ++q) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_addr(&full[q])) : "memory");
+            done_warps[q] = 0u;
+            issued[q] = 0u;
+        }
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+#pragma unroll
+        for (int q = 0; q < kMsStages; ++q) {
+            const int tile = blockIdx.x + q * gridDim.x;
+            if (tile < ntiles) {
+                bulk_load(stage + (size_t)q * SB, a.lt + (size_t)tile * SB, SB, &full[q]);
+                issued[q] = 1u;
+            }
+        }
+    }
+    if (EPI == EPI_A_CG)
+        for (int k = threadIdx.x; k < kMsWarps * kMaxRhs; k += kMsThreads)
+            sysw[k / kMaxRhs][k % kMaxRhs].hi = sysw[k / kMaxRhs][k % kMaxRhs].lo = 0.f;
+    __syncthreads();
+    volatile int *abort = &abort_flag;
+
+    int j = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++j) {
+        const int st = j % kMsStages;
+        const unsigned par = (unsigned)(j / kMsStages) & 1u;
+        const int i = tile * kMTile + site;
+        const bool ok = i < vh;
+        const int iv = ok ? i : vh - 1;  // past Vh: a valid site's fields, zero links, unstored
+        int jf[4], jb[4];
+        T s2f[4], s2b[4];
+        {
+            const Site s = site_of(a.g, iv, a.parity);
+#pragma unroll
+            for (int mu = 0; mu < 4; ++mu) {
+                neighbours(a.g, s, iv, mu, jf[mu], jb[mu]);
+                float sf, sb;
+                link_signs(a.g, s, mu, sf, sb);
+                s2f[mu] = T(sf * LinkPost<P>::row2);
+                s2b[mu] = T(sb * LinkPost<P>::row2);
+            }
+        }
+        const bool ready = mbar_wait(smem_addr(&full[st]), par, abort, &g_ms_wait_timeouts);
+        if (!__syncthreads_and(ready)) break;  // uniform over the CTA
+        const char *sb = stage + (size_t)st * SB;
+
+        for (int k0 = 0; k0 < per; k0 += NB) {
+            int rid[NB];
+            bool run[NB];
+#pragma unroll
+            for (int q = 0; q < NB; ++q) {
+                const int kk = grp + kMsGroups * (k0 + q);
+                run[q] = kk < nact;
+                rid[q] = run[q] ? (a.active ? a.active[kk] : kk) : 0;
+                if (EPI == EPI_GATE || EPI == EPI_A_CG)
+                    run[q] = run[q] && a.states[rid[q]].flag == FLAG_RUN;
+            }
+            Vec3<T> acc[NB];
+            // no branches in the hot loop: a slot that is not running reads
+            // system rid = 0 (valid memory) and its result is dropped below
+            if constexpr (P == PX16) {
+                // systems 2p and 2p + 1 share float2 accumulators: the decode
+                // of the 16-bit fields leaves the FMA pipe the busier one
+                float2 ar[NB / 2][3], ai[NB / 2][3];
+#pragma unroll
+                for (int p2 = 0; p2 < NB / 2; ++p2)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) ar[p2][c] = ai[p2][c] = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int mu = 0; mu < 4; ++mu) {
+                    // both neighbours' fields of every system in flight at once
+                    Vec3<T> vf[NB], vb[NB];
+#pragma unroll
+                    for (int q = 0; q < NB; ++q) {
+                        vf[q] = FieldIO<P>::load_nc(a.in + rid[q] * a.fstride, vh, jf[mu]);
+                        vb[q] = FieldIO<P>::load_nc(a.in + rid[q] * a.fstride, vh, jb[mu]);
+                    }
+                    const Mat3<T> uf = MsLink<P>::load(sb + (size_t)(2 * mu) * LB, site, s2f[mu]);
+#pragma unroll
+                    for (int p2 = 0; p2 < NB / 2; ++p2) {
+                        float2 vr[3], vi[3];
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            vr[c] = make_float2(vf[2 * p2].r[c], vf[2 * p2 + 1].r[c]);
+                            vi[c] = make_float2(vf[2 * p2].i[c], vf[2 * p2 + 1].i[c]);
+                        }
+                        mul_add2(uf, vr, vi, ar[p2], ai[p2]);
+                    }
+                    const Mat3<T> ub = MsLink<P>::load(sb + (size_t)(2 * mu + 1) * LB, site, s2b[mu]);
+#pragma unroll
+                    for (int p2 = 0; p2 < NB / 2; ++p2) {
+                        float2 vr[3], vi[3];
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            vr[c] = make_float2(vb[2 * p2].r[c], vb[2 * p2 + 1].r[c]);
+                            vi[c] = make_float2(vb[2 * p2].i[c], vb[2 * p2 + 1].i[c]);
+                        }
+                        adj_mul_sub2(ub, vr, vi, ar[p2], ai[p2]);
+                    }
+                }
+#pragma unroll
+                for (int p2 = 0; p2 < NB / 2; ++p2)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        acc[2 * p2].r[c] = ar[p2][c].x;
+                        acc[2 * p2].i[c] = ai[p2][c].x;
+                        acc[2 * p2 + 1].r[c] = ar[p2][c].y;
+                        acc[2 * p2 + 1].i[c] = ai[p2][c].y;
+                    }
+            } else {
+                // FP32: scalar FMAs (packing the fields would cost more moves
+                // than it saves)
+#pragma unroll
+                for (int q = 0; q < NB; ++q)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) acc[q].r[c] = acc[q].i[c] = T(0);
+#pragma unroll
+                for (int mu = 0; mu < 4; ++mu) {
+                    Vec3<T> vf[NB], vb[NB];
+#pragma unroll
+                    for (int q = 0; q < NB; ++q) {
+                        vf[q] = FieldIO<P>::load_nc(a.in + rid[q] * a.fstride, vh, jf[mu]);
+                        vb[q] = FieldIO<P>::load_nc(a.in + rid[q] * a.fstride, vh, jb[mu]);
+                    }
+                    const Mat3<T> uf = MsLink<P>::load(sb + (size_t)(2 * mu) * LB, site, T(1));
+#pragma unroll
+                    for (int q = 0; q < NB; ++q) mul_add(uf, vf[q], acc[q], s2f[mu]);
+                    const Mat3<T> ub = MsLink<P>::load(sb + (size_t)(2 * mu + 1) * LB, site, T(1));
+#pragma unroll
+                    for (int q = 0; q < NB; ++q) adj_mul_sub(ub, vb[q], acc[q], s2b[mu]);
+                }
+            }
+            FF dot[NB];
+#pragma unroll
+            for (int q = 0; q < NB; ++q) {
+                dot[q].hi = dot[q].lo = 0.f;
+                if (!ok || !run[q]) continue;
+                if (P == PX16) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        acc[q].r[c] *= T(LinkPost<PX16>::k);
+                        acc[q].i[c] *= T(LinkPost<PX16>::k);
+                    }
+                }
+                char *out = a.out + rid[q] * a.fstride;
+                if (EPI == EPI_NONE || EPI == EPI_GATE) {
+                    FieldIO<P>::store(out, vh, i, acc[q]);
+                } else {
+                    const T m2 = (EPI == EPI_A_CG) ? T(a.states[rid[q]].m2) : T(a.m2[rid[q]]);
+                    const Vec3<T> d = FieldIO<P>::load_nc(a.w + rid[q] * a.fstride, vh, i);
+                    Vec3<T> o;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        o.r[c] = m2 * d.r[c] - acc[q].r[c];
+                        o.i[c] = m2 * d.i[c] - acc[q].i[c];
+                    }
+                    const Vec3<T> os = FieldIO<P>::store(out, vh, i, o);
+                    T dq = T(0);
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) dq += d.r[c] * os.r[c] + d.i[c] * os.i[c];
+                    dot[q].hi = float(dq);
+                }
+            }
+            if (EPI == EPI_A_CG) {
+                // a warp's 32 lanes are sites of one group: the same systems
+#pragma unroll
+                for (int q = 0; q < NB; ++q) {
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) dot[q] = ff_add(dot[q], ff_shfl_down(dot[q], o));
+                    const int kk = grp + kMsGroups * (k0 + q);
+                    if (lane == 0 && kk < nact) sysw[warp][kk] = ff_add(sysw[warp][kk], dot[q]);
+                }
+            }
+        }
+        // release the stage: the last warp to finish refills it
+        __syncwarp();
+        if (lane == 0) {
+            __threadfence_block();
+            if (atomicAdd(&done_warps[st], 1u) == kMsWarps - 1) {
+                done_warps[st] = 0u;
+                const int next = tile + kMsStages * (int)gridDim.x;
+                if (next < ntiles) {
+                    __threadfence_block();
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    bulk_load(stage + (size_t)st * SB, a.lt + (size_t)next * SB, SB, &full[st]);
+                    issued[st] += 1u;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && abort_flag) {
+        // after a timeout, let every copy issued into this CTA land first
+#pragma unroll
+        for (int q = 0; q < kMsStages; ++q)
+            if (issued[q] > 0u) mbar_wait(smem_addr(&full[q]), (issued[q] - 1u) & 1u, nullptr, &g_ms_wait_timeouts);
+    }
+
+    if (EPI == EPI_A_CG) {
+        for (int kk = threadIdx.x; kk < nact; kk += kMsThreads) {
+            FF sum = sysw[0][kk];
+#pragma unroll
+            for (int w = 1; w < kMsWarps; ++w) sum = ff_add(sum, sysw[w][kk]);
+            if (abort_flag) sum.hi = __int_as_float(0x7fc00000);  // the system's sum becomes NaN
+            const int k = a.active ? a.active[kk] : kk;
+            a.partials[(size_t)k * gridDim.x + blockIdx.x] = make_float2(sum.hi, sum.lo);
+        }
+        __threadfence();
+        __syncthreads();
+        __shared__ int is_last;
+        if (threadIdx.x == 0) {
+            __threadfence();
+            const unsigned ticket = atomicAdd(a.counter, 1u);
+            is_last = (ticket == gridDim.x - 1);
+        }
+        __syncthreads();
+        if (!is_last) return;
+        __threadfence();
+        // one warp per system (fixed summation order per system)
+        for (int kk = warp; kk < nact; kk += kMsWarps) {
+            const int k = a.active ? a.active[kk] : kk;
+            if (a.states[k].flag != FLAG_RUN) continue;  // uniform in the warp
+            FF acc = {0.f, 0.f};
+            for (int b = lane; b < (int)gridDim.x; b += 32) {
+                const float2 p = __ldcg(a.partials + (size_t)k * gridDim.x + b);
+                FF t;
+                t.hi = p.x;
+                t.lo = p.y;
+                acc = ff_add(acc, t);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc = ff_add(acc, ff_shfl_down(acc, o));
+            if (lane == 0) {
+                CGState *st = a.states + k;
+                const double total = (double)acc.hi + (double)acc.lo;
+                st->pAp = total;
+                if (!isfinite(total) && *(volatile unsigned *)&g_ms_wait_timeouts) st->flag = FLAG_TIMEOUT;
+                else if (!(total > 0.0) || !isfinite(total)) st->flag = FLAG_BREAKDOWN;
+                else st->alpha = st->delta_new / total;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) *a.counter = 0u;
+    } else if (EPI == EPI_GATE) {
+        if (threadIdx.x == 0 && abort_flag)
+            for (int kk = 0; kk < nact; ++kk) a.states[a.active ? a.active[kk] : kk].flag = FLAG_TIMEOUT;
+    }
+}
+
+// staged shapes: NB = 2, 4, 8 systems per thread and pass
+constexpr int kMrhsStagedShapes = 3;
+__host__ __device__ constexpr int ms_nb(int k) { return k == 0 ? 2 : k == 1 ? 4 : 8; }
+
+template <int P, int NB>
+void launch_ms_nb(int epi, const MrhsArgs &a, cudaStream_t s)
+{
+    constexpr unsigned smem = kMsStages * ms_stage_bytes<P>();
+    static int sms = 0, per_sm = 0;
+    if (!sms) {
+        cudaFuncSetAttribute(k_dslash_ms<P, NB, EPI_NONE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(k_dslash_ms<P, NB, EPI_A>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(k_dslash_ms<P, NB, EPI_GATE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(k_dslash_ms<P, NB, EPI_A_CG>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 148;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dslash_ms<P, NB, EPI_A_CG>, kMsThreads,
+                                                          smem) != cudaSuccess || per_sm < 1)
+            per_sm = 1;
+    }
+    const int ntiles = (a.g.Vh + kMTile - 1) / kMTile;
+    int cap = sms * per_sm;
+    // STG_MRHS_GRID caps the CTA count (more tiles per CTA; for tests)
+    if (const char *v = getenv("STG_MRHS_GRID")) {
+        const int c = atoi(v);
+        if (c > 0 && c < cap) cap = c;
+    }
+    const int grid = ntiles < cap ? ntiles : cap;
+    switch (epi) {
+    case EPI_NONE: k_dslash_ms<P, NB, EPI_NONE><<<grid, kMsThreads, smem, s>>>(a); break;
+    case EPI_A: k_dslash_ms<P, NB, EPI_A><<<grid, kMsThreads, smem, s>>>(a); break;
+    case EPI_GATE: k_dslash_ms<P, NB, EPI_GATE><<<grid, kMsThreads, smem, s>>>(a); break;
+    case EPI_A_CG: k_dslash_ms<P, NB, EPI_A_CG><<<grid, kMsThreads, smem, s>>>(a); break;
+    }
+}
+
+template <int P>
+void launch_ms(int k, int epi, const MrhsArgs &a, cudaStream_t s)
+{
+    if (k == 0) launch_ms_nb<P, 2>(epi, a, s);
+    else if (k == 1) launch_ms_nb<P, 4>(epi, a, s);
+    else launch_ms_nb<P, 8>(epi, a, s);
 }
 
 // (NB, TPS) shapes the autotuner chooses from

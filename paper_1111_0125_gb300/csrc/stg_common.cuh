@@ -568,6 +568,68 @@ __device__ __forceinline__ void adj_mul_sub(const Mat3<T> &u, const Vec3<T> &v, 
 enum CGFlag { FLAG_RUN = 0, FLAG_CONVERGED = 1, FLAG_UPDATE = 2, FLAG_BREAKDOWN = 3,
               FLAG_MAXITER = 4, FLAG_TIMEOUT = 5 };
 
+// ---------------------------------------------------------------------------
+// mbarrier waits with a time limit (bulk async copies into shared memory)
+// ---------------------------------------------------------------------------
+constexpr unsigned long long kWaitLimitNs = 1000000000ull;
+
+__device__ __forceinline__ unsigned smem_addr(const void *p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ bool mbar_try(unsigned bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile("{\n\t.reg .pred p;\n\t"
+                 "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+    return ok != 0u;
+}
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for the phase of the given parity to complete.  Gives up when
+// another thread of the CTA has given up (`abort`, unless null) or after
+// kWaitLimitNs; the first to give up raises `abort` and counts the event in
+// `timeouts`.
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity, volatile int *abort,
+                                          unsigned *timeouts)
+{
+    if (mbar_try(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (;;) {
+        if (mbar_try(bar, parity)) return true;
+        if (abort && *abort) return false;
+        if (global_ns() - t0 > kWaitLimitNs) {
+            if (abort) *abort = 1;
+            atomicAdd(timeouts, 1u);
+            return false;
+        }
+    }
+}
+
+// One bulk async copy global -> shared of `bytes` (16-byte aligned, a
+// multiple of 16) completing on the mbarrier `bar`, which this thread arms
+// with the byte count.  The source is streamed once: L2 evicts it first.
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes, unsigned long long *bar)
+{
+    const unsigned b = smem_addr(bar);
+    unsigned long long pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(b), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint "
+                 "[%0], [%1], %2, [%3], %4;"
+                 :: "r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(b), "l"(pol)
+                 : "memory");
+}
+
 // Programmatic dependent launch: pdl_wait() returns once the preceding
 // kernel of the stream has completed and its writes are visible (at once when
 // the kernel was launched without the attribute); pdl_trigger() lets the next

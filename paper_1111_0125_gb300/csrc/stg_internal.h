@@ -43,6 +43,14 @@ static inline cudaError_t launch_k(void (*kernel)(K...), dim3 grid, dim3 block, 
 constexpr int kFxTile = 1024;
 constexpr unsigned kFxStageBytes = kFxTile * 48u;
 
+// Tile-major copy of FP32 / 12-real and FX16 / 12-real links for the staged
+// multi-system Dslash: for output parity p and tile k of kMTile consecutive
+// output sites, one contiguous block of kMTile * 8 * L bytes holds, for mu =
+// 0..3 and dir = forward, backward, the 12-real records of the tile's sites
+// as planes (FP32: three float4 planes; FX16: a uint4 plane then a uint2
+// plane); slots past Vh are zero.
+constexpr int kMTile = 64;
+
 struct LinkField {
     char *base = nullptr;   // 8 blocks: (parity, mu) -> base + (2 * 4 ... ) see blk()
     int prec = -1;
@@ -50,6 +58,8 @@ struct LinkField {
     size_t blk_bytes = 0;   // bytes of one (parity, mu) block, 256-aligned
     char *tiled = nullptr;  // FX16 / 12-real only: tile-major copy (kFxTile)
     size_t tiled_parity_bytes = 0;
+    char *mtiled = nullptr; // 12-real FP32 / FX16: tile-major copy (kMTile)
+    size_t mtiled_parity_bytes = 0, mtile_bytes = 0;
     const char *blk(int parity, int mu) const { return base + (size_t)(parity * 4 + mu) * blk_bytes; }
 };
 

@@ -58,7 +58,10 @@ def test_dslash_mrhs_matches_oracle_and_single(dims, prec, recon, n):
                 # differently in the two kernels, so agreement is to rounding
                 assert rel(got[k], single) < TOL[prec]
         nb, tps = stg.stg_mrhs_tuning(g.handle, prec, n)
-        assert nb in (1, 2, 4) and tps in (1, 2, 4, 8, 16) and tps <= max(1, n)
+        if tps == 0:  # staged kernel (12-real only)
+            assert recon == 12 and nb in (2, 4, 8)
+        else:
+            assert nb in (1, 2, 4) and tps in (1, 2, 4, 8, 16) and tps <= max(1, n)
 
 
 @pytest.mark.parametrize("prec", [stg.STG_FP32, stg.STG_FX16])
@@ -75,6 +78,47 @@ def test_apply_A_mrhs_per_system_masses(prec):
         ins = _unpack_batch(g, buf, fb, n, prec)
     for k in range(n):
         assert rel(got[k], oracle.apply_A(dims, U, masses[k], ins[k])) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [stg.STG_FP32, stg.STG_FX16])
+@pytest.mark.parametrize("shape,nb", [("9", 2), ("10", 4), ("11", 8)])
+@pytest.mark.parametrize("grid", [None, "2"])
+def test_staged_mrhs_matches_register_fed(monkeypatch, prec, shape, nb, grid):
+    """The staged multi-system kernel (links of a 64-site tile in shared
+    memory, shared by every system) against the register-fed kernel and the
+    oracle, for each register block NB; a grid of 2 CTAs makes each CTA walk
+    12 of the 23 tiles (ragged last tile) through its 3-stage ring."""
+    dims, n = (6, 4, 10, 12), 9
+    U = gen.gauge_field(dims, "exp", seed=6, eps=0.5)
+    chis = list(gen.source(dims, seed=8, nrhs=n))
+    masses = gen.log_uniform(n, 0.005, 0.05, seed=10)
+    with stg.Gauge(dims, U, sloppy=prec, recon=12) as g:
+        buf, fb = _pack_batch(g, chis, prec)
+        ins = _unpack_batch(g, buf, fb, n, prec)
+        monkeypatch.setenv("STG_MRHS_SHAPE", "2")  # register-fed, NB = 4
+        ref = torch.empty_like(buf)
+        stg.stg_dslash_mrhs(g.handle, 1, n, buf, ref, prec)
+        ref = _unpack_batch(g, ref, fb, n, prec)
+        monkeypatch.setenv("STG_MRHS_SHAPE", shape)
+        if grid is not None:
+            monkeypatch.setenv("STG_MRHS_GRID", grid)
+        for parity in (0, 1):
+            out = torch.empty_like(buf)
+            stg.stg_dslash_mrhs(g.handle, parity, n, buf, out, prec)
+            got = _unpack_batch(g, out, fb, n, prec)
+            for k in range(n):
+                assert rel(got[k], oracle.dslash(dims, U, ins[k], parity)) < TOL[prec], (k, parity)
+                if parity == 1:
+                    assert rel(got[k], ref[k]) < TOL[prec], k
+        out = torch.empty_like(buf)
+        stg.stg_apply_A_mrhs(g.handle, n, masses, buf, out, prec)
+        got = _unpack_batch(g, out, fb, n, prec)
+        for k in range(n):
+            assert rel(got[k], oracle.apply_A(dims, U, masses[k], ins[k])) < TOL[prec], k
+        xs, st = _solve_batch(g, chis, masses, 1e-10, prec)
+        for k in range(n):
+            r = chis[k] - oracle.apply_A(dims, U, masses[k], xs[k])
+            assert np.linalg.norm(r) <= 1e-10 * np.linalg.norm(chis[k]), k
 
 
 def _solve_batch(g, bs, masses, tol, sloppy, policy=stg.STG_CG_RELIABLE):
