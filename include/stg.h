@@ -158,6 +158,12 @@ stg_status stg_gauge_create(const int dims[4], const double *links_host,
                             stg_prec sloppy, int recon, stg_stream_t stream,
                             stg_gauge **out);
 
+/* Device bytes that a handle created with these arguments keeps resident
+ * (FP64 links, the sloppy links and their tile-major copies; the solver
+ * workspace comes on top).  During stg_gauge_create a further 576 V bytes
+ * (the canonical links) are held for the upload.  0 for invalid arguments. */
+size_t stg_gauge_bytes(const int dims[4], stg_prec sloppy, int recon);
+
 /* Free the handle, its device links and its workspace.  NULL is a no-op. */
 stg_status stg_gauge_destroy(stg_gauge *g);
 

@@ -76,6 +76,7 @@ def _load():
         "stg_last_error": (ctypes.c_char_p, []),
         "stg_gauge_create": (i, [p, p, i, i, p, p]),
         "stg_gauge_destroy": (i, [p]),
+        "stg_gauge_bytes": (sz, [p, i, i]),
         "stg_gauge_dims": (i, [p, p, p]),
         "stg_field_bytes": (i, [p, i, p]),
         "stg_pack_field": (i, [p, i, p, p, p]),
@@ -292,6 +293,12 @@ def stg_batch_step(batch: int, max_done: int = 64):
     _check(lib.stg_batch_step(batch, int(max_done), slots, status, stats, ctypes.byref(n_done),
                               ctypes.byref(n_act)), "stg_batch_step")
     return ([(slots[k], status[k], stats[k].as_dict()) for k in range(n_done.value)], n_act.value)
+
+
+def stg_gauge_bytes(dims, sloppy: int, recon: int) -> int:
+    """Device bytes a handle with these arguments keeps resident (0: invalid)."""
+    d = (ctypes.c_int * 4)(*[int(v) for v in dims])
+    return int(lib.stg_gauge_bytes(d, int(sloppy), int(recon)))
 
 
 def stg_batch_bytes(handle: int, max_systems: int, sloppy: int) -> int:

@@ -24,6 +24,7 @@ stg_status cuda_fail(cudaError_t e, const char *what)
 stg_status gauge_create(const int dims[4], const double *links_host, int sloppy, int recon,
                         cudaStream_t s, stg_gauge **out);
 void gauge_destroy(stg_gauge *g);
+size_t gauge_bytes(const int dims[4], int sloppy, int recon);
 stg_status pack_field(const Geom &g, int prec, const double *canon, void *out, cudaStream_t s);
 stg_status unpack_field(const Geom &g, int prec, const void *in, double *canon, cudaStream_t s);
 stg_status cg_solve(stg_gauge *g, const double *src, double *x, double mass, double tol,
@@ -123,6 +124,12 @@ stg_status stg_gauge_create(const int dims[4], const double *links_host, stg_pre
     }
     *out = nullptr;
     return gauge_create(dims, links_host, sloppy, recon, (cudaStream_t)stream, out);
+}
+
+size_t stg_gauge_bytes(const int dims[4], stg_prec sloppy, int recon)
+{
+    if (check_dims(dims) != STG_OK || !valid_prec(sloppy) || (recon != 18 && recon != 12)) return 0;
+    return gauge_bytes(dims, sloppy, recon);
 }
 
 stg_status stg_gauge_destroy(stg_gauge *g)

@@ -348,6 +348,20 @@ const LinkField *links_for(const stg_gauge *g, int prec)
     return nullptr;
 }
 
+size_t gauge_bytes(const int dims[4], int sloppy, int recon)
+{
+    const Geom g = make_geom(dims);
+    const size_t vh = (size_t)g.Vh;
+    const int recon_hi = (sloppy == P64) ? recon : 18;
+    size_t n = 8 * align256(vh * link_bytes(P64, recon_hi));
+    if (sloppy != P64) n += 8 * align256(vh * link_bytes(sloppy, recon));
+    if (sloppy == PX16 && recon == 12 && want_tiled())
+        n += 2 * (size_t)((g.Vh + kFxTile - 1) / kFxTile) * 4 * kFxStageBytes;
+    if ((sloppy == P32 || sloppy == PX16) && recon == 12 && want_mtiled())
+        n += 2 * (size_t)((g.Vh + kMTile - 1) / kMTile) * kMTile * 8 * (sloppy == P32 ? 48 : 24);
+    return n;
+}
+
 stg_status gauge_create(const int dims[4], const double *links_host, int sloppy, int recon,
                         cudaStream_t s, stg_gauge **out)
 {

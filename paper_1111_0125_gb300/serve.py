@@ -30,7 +30,7 @@ import numpy as np
 import torch
 
 from . import (STG_FP32, STG_OK, stg_batch_add, stg_batch_bytes, stg_batch_create,
-               stg_batch_destroy, stg_batch_step, stg_cg_params_default)
+               stg_batch_destroy, stg_batch_step, stg_cg_params_default, stg_gauge_bytes)
 from .fields import Gauge
 
 
@@ -60,10 +60,11 @@ class Result:
         return self.done - self.arrival
 
 
-def gauge_bytes(dims, recon: int = 12, sloppy_link_bytes: int = 48) -> int:
-    """Device bytes of a handle: FP64/18 links plus the sloppy links."""
-    v = int(np.prod(dims))
-    return v // 2 * 8 * (144 + sloppy_link_bytes) + 4096
+def gauge_bytes(dims, sloppy: int = STG_FP32, recon: int = 12) -> int:
+    """Device bytes a handle keeps resident (the library's own count: FP64
+    links, sloppy links and their tile-major copies) plus its workspace
+    scalars."""
+    return stg_gauge_bytes(dims, sloppy, recon) + 4096
 
 
 class _Session:
@@ -198,7 +199,7 @@ class ServeEngine:
         if e is not None:
             return e
         dims, links = self.gauge_src[key]
-        need = gauge_bytes(dims)
+        need = gauge_bytes(dims, self.sloppy, self.recon)
         # evict idle gauges while over the resident count or the budget
         while (len(self.resident) >= self.max_resident or self.used + need > self.budget):
             idle = [g for g in self.resident.values() if all(s.load() == 0 for s in g.sessions)]

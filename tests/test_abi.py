@@ -89,3 +89,29 @@ def test_product_path_never_imports_the_oracle():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "stg_oracle" not in text and "liboracle" not in text, f
+
+
+def test_gauge_bytes_counts_every_link_copy(stg, monkeypatch):
+    """Resident bytes of a handle (host arithmetic, no GPU): FP64/18 links,
+    the sloppy links, and the tile-major copies of 12-real sloppy links (64-
+    site tiles for the multi-system kernel; 1024-site tiles of four 48 KB
+    stages for the single-system FX16 kernel)."""
+    def a256(n):
+        return (n + 255) // 256 * 256
+
+    dims = (24, 24, 24, 48)
+    vh = 24 * 24 * 24 * 48 // 2
+    hi = 8 * a256(vh * 144)
+    assert stg.stg_gauge_bytes(dims, stg.STG_FP64, 18) == hi
+    assert stg.stg_gauge_bytes(dims, stg.STG_FP64, 12) == 8 * a256(vh * 96)
+    mt32 = 2 * (-(-vh // 64)) * 64 * 8 * 48
+    assert stg.stg_gauge_bytes(dims, stg.STG_FP32, 12) == hi + 8 * a256(vh * 48) + mt32
+    assert stg.stg_gauge_bytes(dims, stg.STG_FP32, 18) == hi + 8 * a256(vh * 72)
+    fx = 2 * (-(-vh // 1024)) * 4 * 1024 * 48
+    mtx = 2 * (-(-vh // 64)) * 64 * 8 * 24
+    assert stg.stg_gauge_bytes(dims, stg.STG_FX16, 12) == hi + 8 * a256(vh * 24) + fx + mtx
+    monkeypatch.setenv("STG_FX16_TILED", "0")
+    monkeypatch.setenv("STG_MRHS_TILED", "0")
+    assert stg.stg_gauge_bytes(dims, stg.STG_FX16, 12) == hi + 8 * a256(vh * 24)
+    assert stg.stg_gauge_bytes((4, 4, 3, 4), stg.STG_FP32, 12) == 0
+    assert stg.stg_gauge_bytes(dims, stg.STG_FP32, 10) == 0
