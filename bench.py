@@ -64,6 +64,10 @@ def parse():
     ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--load", type=float, default=0.7,
                     help="c5: offered rate as a fraction of the measured saturation rate")
+    ap.add_argument("--no-priority", action="store_true",
+                    help="c5: every session on a default-priority stream")
+    ap.add_argument("--sweep", type=float, nargs="*", default=[0.3, 0.5],
+                    help="c5: further offered loads (fractions of saturation) to report")
     ap.add_argument("--nrhs", type=int, default=16)
     ap.add_argument("--reps", type=int, default=3)
     return ap.parse_args()
@@ -393,15 +397,25 @@ def run_c5(args):
             sources[(li, j)] = gen.source(dims, seed=1000 + 10 * li + j)
     sloppy = {"f32": stg.STG_FP32, "fx16": stg.STG_FX16}[args.sloppy]
     eng = ServeEngine(gauges, sources, hbm_budget=120e9, slots=8, max_sessions_per_gauge=2,
-                      max_resident=8, sloppy=sloppy, recon=args.recon)
+                      max_resident=8, sloppy=sloppy, recon=args.recon,
+                      priority_by_size=not args.no_priority)
     try:
         eng.run(c5_requests(64, None, seed=7), realtime=False)       # warm-up, tuning
         sat_res = eng.run(c5_requests(args.requests, None), realtime=False)
         sat = summarize(sat_res)
-        rate = args.load * sat["solves_per_s"]
-        clocks = ClockSampler("")
-        res = eng.run(c5_requests(args.requests, rate), realtime=True)
-        ck = clocks.stop()
+        # the offered rate swept below the saturation throughput; the
+        # headline is args.load (0.7)
+        sweep = []
+        for load in sorted({*args.sweep, args.load}):
+            r_ = load * sat["solves_per_s"]
+            clocks = ClockSampler("")
+            res_ = eng.run(c5_requests(args.requests, r_), realtime=True)
+            ck_ = clocks.stop()
+            sm_ = summarize(res_)
+            sweep.append({"load": load, "offered_rate": r_, "solves_per_s": sm_["solves_per_s"],
+                          "p50_ms": sm_["p50_ms"], "p99_ms": sm_["p99_ms"], "ok": sm_["ok"]})
+            if load == args.load:
+                res, rate, ck = res_, r_, ck_
     finally:
         eng.close()
     summ = summarize(res)
@@ -422,10 +436,11 @@ def run_c5(args):
                    "gauge_fields": 8, "sources_per_lattice": 4,
                    "mass": "log-uniform [0.005, 0.1]", "tol": "1e-8 or 1e-10",
                    "hbm_budget_gb": 120, "slots_per_session": 8, "sessions_per_gauge": 2,
+                   "stream_priority_by_lattice_size": not args.no_priority,
                    "sloppy_storage": args.sloppy, "offered_rate": rate,
                    "load_vs_saturation": args.load},
         "p50_ms": summ["p50_ms"], "p99_ms": summ["p99_ms"], "mean_ms": summ["mean_ms"],
-        "ok": summ["ok"], "saturation": sat, "per_lattice": per,
+        "ok": summ["ok"], "saturation": sat, "load_sweep": sweep, "per_lattice": per,
         "max_true_res_over_tol": max(r.true_res / q.tol for r, q in zip(res, reqs)),
         "clocks": ck,
     }), flush=True)

@@ -16,6 +16,11 @@ session created only while the budget allows; otherwise the request waits
 until memory frees.  Latency is measured per request from its arrival to the
 moment its solution is back in host memory.
 
+With `priority_by_size`, sessions of smaller lattices run on higher-priority
+CUDA streams, so their short kernels are scheduled ahead of the long
+kernels of large lattices (shortest job first at the level of thread
+blocks); the largest lattice keeps the default priority.
+
 This module only schedules: every solve runs in the CUDA library through the
 C ABI.
 """
@@ -70,10 +75,10 @@ def gauge_bytes(dims, sloppy: int = STG_FP32, recon: int = 12) -> int:
 class _Session:
     """One batch session on one resident gauge field, driven by a thread."""
 
-    def __init__(self, engine, entry, device):
+    def __init__(self, engine, entry, device, priority=0):
         self.engine = engine
         self.entry = entry
-        self.stream = torch.cuda.Stream(device=device)
+        self.stream = torch.cuda.Stream(device=device, priority=priority)
         params = stg_cg_params_default(entry.gauge.handle)
         params.sloppy = engine.sloppy
         params.check_every = engine.chunk
@@ -161,7 +166,8 @@ class ServeEngine:
 
     def __init__(self, gauges: dict, sources: dict, hbm_budget: float = 120e9, slots: int = 8,
                  max_sessions_per_gauge: int = 2, max_resident: int = 8, sloppy: int = STG_FP32,
-                 recon: int = 12, chunk: int = 16, keep_solutions: bool = False, device: int = 0):
+                 recon: int = 12, chunk: int = 16, keep_solutions: bool = False, device: int = 0,
+                 priority_by_size: bool = True):
         self.gauge_src = gauges
         self.sources = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory()
                         for k, v in sources.items()}
@@ -174,6 +180,11 @@ class ServeEngine:
         self.chunk = chunk
         self.keep_solutions = keep_solutions
         self.device = device
+        self.priority_by_size = priority_by_size
+        vols = sorted({int(np.prod(d)) for d, _ in gauges.values()})
+        # stream priority per lattice volume: 0 for the largest, one step
+        # higher (more negative) per distinct larger volume
+        self._prio = {v: -(len(vols) - 1 - k) for k, v in enumerate(vols)}
         self.used = 0.0
         self.resident: dict = {}
         self.results: list = []
@@ -234,7 +245,10 @@ class ServeEngine:
             need = stg_batch_bytes(e.gauge.handle, self.slots, self.sloppy) + \
                 2 * self.slots * e.gauge.vh * 48
             if self.used + need <= self.budget:
-                s = _Session(self, e, self.device)
+                prio = 0
+                if self.priority_by_size:
+                    prio = self._prio.get(int(np.prod(self.gauge_src[e.key][0])), 0)
+                s = _Session(self, e, self.device, prio)
                 self.used += s.bytes
                 e.sessions.append(s)
                 s.submit(req)
