@@ -323,13 +323,14 @@ __global__ void __launch_bounds__(kBlock, STG_FX2_MINBLOCKS) k_dslash_fx2(const 
 // Staged variant (12-real links from the tile-major copy).  The eight links
 // of an output site sit at that site's slot, so the links of one tile of
 // kFxTile output sites and one direction mu are a single contiguous block of
-// 48 KB.  One CTA of 16 warps per SM keeps a ring of four shared-memory
-// stages, one per mu, filled by bulk async copies (cp.async.bulk) whose
-// arrival an mbarrier counts in bytes; the threads compute two sites each
-// exactly as k_dslash_fx2 does, reading the links from shared memory.  The
-// warp that finishes reading stage mu last (a shared-memory arrival count)
-// refills it with the CTA's next tile, so there is no producer warp and the
-// 16 warps keep 128 registers each.  Up to three 48 KB stages per SM are in
+// 48 KB.  One CTA of 16 warps per SM keeps a ring of kFxStages shared-memory
+// stages through which the CTA's (tile, mu) items pass in order, filled by
+// bulk async copies (cp.async.bulk) whose arrival an mbarrier counts in
+// bytes; the threads compute two sites each exactly as k_dslash_fx2 does,
+// reading the links from shared memory.  The warp that finishes reading a
+// stage last (a shared-memory arrival count) refills it with the item
+// kFxStages further on, so there is no producer warp and the 16 warps keep
+// 128 registers each.  Up to kFxStages - 1 items of 48 KB per SM are in
 // flight, independent of the registers that capped the loads in flight of
 // the register-fed kernel.
 //
@@ -341,26 +342,30 @@ __global__ void __launch_bounds__(kBlock, STG_FX2_MINBLOCKS) k_dslash_fx2(const 
 constexpr int kFxCons = kFxTile / 2;       // threads, two sites each
 constexpr int kFxConsWarps = kFxCons / 32;
 constexpr int kFxCtasPerSM = 1024 / kFxTile;  // 16 warps of 128 registers per SM
-constexpr unsigned kFxSmem = 4 * kFxStageBytes;
+#ifndef STG_FX_STAGES
+#define STG_FX_STAGES 4
+#endif
+constexpr int kFxStages = STG_FX_STAGES;  // ring of (tile, mu) stages
+constexpr unsigned kFxSmem = kFxStages * kFxStageBytes;
 
 __device__ unsigned g_fx_wait_timeouts;
 
-// fill stage mu with the links of (tile, mu); one thread.  Links are read
-// once per half-pass: L2 evicts them first, so the fields that the CG
+// fill ring stage st with the links of (tile, mu); one thread.  Links are
+// read once per half-pass: L2 evicts them first, so the fields that the CG
 // kernels re-read stay resident.
-__device__ __forceinline__ void fill_stage(const char *lt, char *stage, unsigned long long *full, int tile,
-                                           int mu)
+__device__ __forceinline__ void fill_stage(const char *lt, char *stage, unsigned long long *full, int st,
+                                           int tile, int mu)
 {
-    bulk_load(stage + (size_t)mu * kFxStageBytes, lt + ((size_t)tile * 4 + mu) * kFxStageBytes, kFxStageBytes,
-              &full[mu]);
+    bulk_load(stage + (size_t)st * kFxStageBytes, lt + ((size_t)tile * 4 + mu) * kFxStageBytes, kFxStageBytes,
+              &full[st]);
 }
 
 template <int EPI>
 __global__ void __launch_bounds__(kFxCons, kFxCtasPerSM) k_dslash_fx2_staged(const DslashArgs a)
 {
     extern __shared__ __align__(128) char stage[];
-    __shared__ __align__(8) unsigned long long full[4];
-    __shared__ unsigned done_warps[4], issued[4];
+    __shared__ __align__(8) unsigned long long full[kFxStages];
+    __shared__ unsigned done_warps[kFxStages], issued[kFxStages];
     __shared__ int abort_flag;
     const int vh = a.g.Vh;
     const int ntiles = (vh + kFxTile - 1) / kFxTile;
@@ -370,19 +375,27 @@ __global__ void __launch_bounds__(kFxCons, kFxCtasPerSM) k_dslash_fx2_staged(con
     // decides whether to prefetch; the check after the wait decides.
     const bool prefetch = (EPI != EPI_A_CG && EPI != EPI_GATE) ||
                           *(volatile const int *)&a.state->flag == FLAG_RUN;
+    // the (tile, mu) items of this CTA in order, item q = 4 j + mu, go
+    // round the ring: stage q % kFxStages, fill q / kFxStages of that stage
     if (c == 0) {
 #pragma unroll
-        for (int mu = 0; mu < 4; ++mu) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_addr(&full[mu])) : "memory");
-            done_warps[mu] = 0u;
-            issued[mu] = prefetch ? 1u : 0u;
+        for (int q = 0; q < kFxStages; ++q) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_addr(&full[q])) : "memory");
+            done_warps[q] = 0u;
+            issued[q] = 0u;
         }
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         if (prefetch) {
 #pragma unroll
-            for (int mu = 0; mu < 4; ++mu) fill_stage(a.lt, stage, full, blockIdx.x, mu);
+            for (int q = 0; q < kFxStages; ++q) {
+                const int tq = blockIdx.x + (q / 4) * gridDim.x;
+                if (tq < ntiles) {
+                    fill_stage(a.lt, stage, full, q, tq, q % 4);
+                    issued[q] = 1u;
+                }
+            }
         }
     }
     __syncthreads();
@@ -391,16 +404,22 @@ __global__ void __launch_bounds__(kFxCons, kFxCtasPerSM) k_dslash_fx2_staged(con
     pdl_trigger();
     if (EPI == EPI_A_CG || EPI == EPI_GATE) {
         if (a.state->flag != FLAG_RUN) {  // uniform over the grid
-            if (c == 0 && prefetch) {
+            if (c == 0) {
 #pragma unroll
-                for (int mu = 0; mu < 4; ++mu) mbar_wait(smem_addr(&full[mu]), 0u, nullptr, &g_fx_wait_timeouts);
+                for (int q = 0; q < kFxStages; ++q)
+                    if (issued[q]) mbar_wait(smem_addr(&full[q]), 0u, nullptr, &g_fx_wait_timeouts);
             }
             return;
         }
         if (!prefetch && c == 0) {  // the flag was lowered after the early read
 #pragma unroll
-            for (int mu = 0; mu < 4; ++mu) fill_stage(a.lt, stage, full, blockIdx.x, mu);
-            for (int mu = 0; mu < 4; ++mu) issued[mu] = 1u;
+            for (int q = 0; q < kFxStages; ++q) {
+                const int tq = blockIdx.x + (q / 4) * gridDim.x;
+                if (tq < ntiles) {
+                    fill_stage(a.lt, stage, full, q, tq, q % 4);
+                    issued[q] = 1u;
+                }
+            }
         }
         __syncthreads();
     }
@@ -437,12 +456,15 @@ __global__ void __launch_bounds__(kFxCons, kFxCtasPerSM) k_dslash_fx2_staged(con
             Vec3x2 vf, vb;
             load_field2(a.in, jfA, jfB, vf);
             load_field2(a.in, jbA, jbB, vb);
-            const bool ready = mbar_wait(smem_addr(&full[mu]), j & 1, abort, &g_fx_wait_timeouts);
+            const int q = 4 * j + mu;          // item number
+            const int sq = q % kFxStages;      // its ring stage
+            const bool ready = mbar_wait(smem_addr(&full[sq]), (unsigned)(q / kFxStages) & 1u, abort,
+                                         &g_fx_wait_timeouts);
             if (!__all_sync(0xffffffffu, ready)) {
                 alive = false;
                 break;
             }
-            const char *st = stage + (size_t)mu * kFxStageBytes;
+            const char *st = stage + (size_t)sq * kFxStageBytes;
             const uint4 *f16 = reinterpret_cast<const uint4 *>(st);
             const uint2 *f8 = reinterpret_cast<const uint2 *>(st + 16 * kFxTile);
             const uint4 *b16 = reinterpret_cast<const uint4 *>(st + 24 * kFxTile);
@@ -456,13 +478,15 @@ __global__ void __launch_bounds__(kFxCons, kFxCtasPerSM) k_dslash_fx2_staged(con
             __syncwarp();
             if (lane == 0) {
                 __threadfence_block();
-                if (atomicAdd(&done_warps[mu], 1u) == kFxConsWarps - 1) {
-                    done_warps[mu] = 0u;
-                    if (tile + (int)gridDim.x < ntiles && !(a.drop_fill && j == 0 && mu == 0)) {
+                if (atomicAdd(&done_warps[sq], 1u) == kFxConsWarps - 1) {
+                    done_warps[sq] = 0u;
+                    const int qn = q + kFxStages;  // the item this stage holds next
+                    const int tn = blockIdx.x + (qn / 4) * (int)gridDim.x;
+                    if (tn < ntiles && !(a.drop_fill && qn == 4)) {
                         __threadfence_block();
                         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                        fill_stage(a.lt, stage, full, tile + gridDim.x, mu);
-                        issued[mu] += 1u;
+                        fill_stage(a.lt, stage, full, sq, tn, qn % 4);
+                        issued[sq] += 1u;
                     }
                 }
             }
@@ -498,7 +522,8 @@ __global__ void __launch_bounds__(kFxCons, kFxCtasPerSM) k_dslash_fx2_staged(con
     if (c == 0 && abort_flag) {
         // after a timeout, let every copy issued into this CTA land first
 #pragma unroll
-        for (int mu = 0; mu < 4; ++mu) mbar_wait(smem_addr(&full[mu]), (issued[mu] - 1u) & 1u, nullptr, &g_fx_wait_timeouts);
+        for (int q = 0; q < kFxStages; ++q)
+            if (issued[q]) mbar_wait(smem_addr(&full[q]), (issued[q] - 1u) & 1u, nullptr, &g_fx_wait_timeouts);
         if (EPI == EPI_GATE) a.state->flag = FLAG_TIMEOUT;  // no grid sum here
     }
     if (EPI == EPI_A_DOT || EPI == EPI_A_CG || EPI == EPI_RES) {

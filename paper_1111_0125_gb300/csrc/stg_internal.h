@@ -171,8 +171,9 @@ struct DslashArgs {
     const char *lf[4];  // forward link blocks  (parity p,   mu)
     const char *lb[4];  // backward link blocks (parity 1-p, mu)
     const char *lt;     // tile-major links of output parity p (FX16 / 12), or null
-    int drop_fill;      // tests only: the staged kernel withholds its second
-                        // fill of stage 0, so that bounded wait runs out
+    int drop_fill;      // tests only: the staged kernel withholds the fill of
+                        // its second tile's first stage, so that bounded
+                        // wait runs out
     int parity;
     const void *in;
     void *out;
