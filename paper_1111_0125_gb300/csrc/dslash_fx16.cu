@@ -545,17 +545,15 @@ __global__ void __launch_bounds__(kFxCons, kFxCtasPerSM) k_dslash_fx2_staged(con
 template <int EPI>
 static void launch_staged(const DslashArgs &a, cudaStream_t s, bool pdl)
 {
-    static int sms = 0;
-    static bool attr = false;
-    if (!attr) {
+    // set once per instantiation (thread-safe static initialisation)
+    static const int sms = [] {
         cudaFuncSetAttribute(k_dslash_fx2_staged<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)kFxSmem);
-        int dev = 0;
+        int dev = 0, n = 0;
         cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 148;
-        attr = true;
-    }
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
+        return n;
+    }();
     // STG_FX16_GRID caps the CTA count (more tiles per CTA; for tests)
     int cap = sms * kFxCtasPerSM;
     if (const char *v = getenv("STG_FX16_GRID")) {

@@ -102,13 +102,12 @@ static void tune_store(const int *dims, int prec, int recon, int nrhs, int shape
 
 static int num_sms_m()
 {
-    static int n = 0;
-    if (n == 0) {
-        int dev = 0;
+    static const int n = [] {
+        int dev = 0, m = 0;
         cudaGetDevice(&dev);
-        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
-            n = 148;
-    }
+        if (cudaDeviceGetAttribute(&m, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || m <= 0) m = 148;
+        return m;
+    }();
     return n;
 }
 

@@ -621,22 +621,24 @@ template <int P, int NB>
 void launch_ms_nb(int epi, const MrhsArgs &a, cudaStream_t s)
 {
     constexpr unsigned smem = kMsStages * ms_stage_bytes<P>();
-    static int sms = 0, per_sm = 0;
-    if (!sms) {
+    // set once per instantiation (thread-safe static initialisation):
+    // resident CTAs on the whole GPU
+    static const int resident = [] {
         cudaFuncSetAttribute(k_dslash_ms<P, NB, EPI_NONE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         cudaFuncSetAttribute(k_dslash_ms<P, NB, EPI_A>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         cudaFuncSetAttribute(k_dslash_ms<P, NB, EPI_GATE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         cudaFuncSetAttribute(k_dslash_ms<P, NB, EPI_A_CG>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        int dev = 0;
+        int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 148;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+            sms = 148;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dslash_ms<P, NB, EPI_A_CG>, kMsThreads,
                                                           smem) != cudaSuccess || per_sm < 1)
             per_sm = 1;
-    }
+        return sms * per_sm;
+    }();
     const int ntiles = (a.g.Vh + kMTile - 1) / kMTile;
-    int cap = sms * per_sm;
+    int cap = resident;
     // STG_MRHS_GRID caps the CTA count (more tiles per CTA; for tests)
     if (const char *v = getenv("STG_MRHS_GRID")) {
         const int c = atoi(v);
