@@ -34,8 +34,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 LINK_BYTES = {("f64", 18): 144, ("f64", 12): 96, ("f32", 18): 72, ("f32", 12): 48,
-              ("f16", 18): 36, ("f16", 12): 24, ("fx16", 18): 36, ("fx16", 12): 24}
-FIELD_BYTES = {"f64": 48, "f32": 24, "f16": 16, "fx16": 16}
+              ("f16", 18): 36, ("f16", 12): 24, ("fx16", 18): 36, ("fx16", 12): 24,
+              ("bf16", 18): 36, ("bf16", 12): 24}
+FIELD_BYTES = {"f64": 48, "f32": 24, "f16": 16, "fx16": 16, "bf16": 16}
 FALLBACK_HBM_GBS = 6800.0
 WORKLOAD = "32^3x64 staggered mixed-precision CG to 1e-10 true residual"
 
@@ -47,7 +48,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="stg", choices=["stg", "reference"])
     ap.add_argument("--lattice", default="32,32,32,64")
-    ap.add_argument("--sloppy", default="fx16", choices=["f32", "f16", "fx16"])
+    ap.add_argument("--sloppy", default="fx16", choices=["f32", "f16", "fx16", "bf16"])
     ap.add_argument("--recon", type=int, default=12, choices=[12, 18])
     ap.add_argument("--mass", type=float, default=0.005)
     ap.add_argument("--tol", type=float, default=1e-10)
@@ -472,7 +473,8 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
-    sloppy = {"f32": stg.STG_FP32, "f16": stg.STG_FP16, "fx16": stg.STG_FX16}[args.sloppy]
+    sloppy = {"f32": stg.STG_FP32, "f16": stg.STG_FP16, "fx16": stg.STG_FX16,
+              "bf16": stg.STG_BF16}[args.sloppy]
     U, b_np = gen_inputs(dims, args.eps, rank)
     vh = b_np.shape[0]
     g = stg.Gauge(dims, U, sloppy=sloppy, recon=args.recon)

@@ -75,12 +75,13 @@ typedef enum stg_status {
 } stg_status;
 
 /* Storage precision of links and fields.  FP64 and FP32 compute in their own
- * precision; FP16 (IEEE binary16) and FX16 (16-bit fixed point) store 16-bit
- * values and compute in FP32.  Fields of both 16-bit kinds carry one FP32
- * scale per site (the largest |re| or |im| of the site's colour vector);
- * FX16 links use the fixed scale 1/32767 and so require |U_ab| <= 1, which
- * holds for SU(3). */
-typedef enum stg_prec { STG_FP64 = 0, STG_FP32 = 1, STG_FP16 = 2, STG_FX16 = 3 } stg_prec;
+ * precision; FP16 (IEEE binary16), BF16 (bfloat16) and FX16 (16-bit fixed
+ * point) store 16-bit values and compute in FP32.  Fields of the 16-bit kinds
+ * carry one FP32 scale per site (the largest |re| or |im| of the site's
+ * colour vector); FX16 links use the fixed scale 1/32767 and so require
+ * |U_ab| <= 1, which holds for SU(3).  BF16 keeps 8 significand bits (unit
+ * round-off 2^-8): its Dslash error is about 3e-3, above FP16's 2e-3. */
+typedef enum stg_prec { STG_FP64 = 0, STG_FP32 = 1, STG_FP16 = 2, STG_FX16 = 3, STG_BF16 = 4 } stg_prec;
 
 typedef enum stg_cg_policy {
     STG_CG_RELIABLE = 0, /* Sec. 3.2: Eq. 6 start, reliable + group-wise update */
@@ -173,8 +174,8 @@ stg_status stg_gauge_dims(const stg_gauge *g, int dims[4], long *vh);
 /*
  * Bytes of one checkerboard field (Vh sites, 3 colours) in the device layout
  * of `prec`: FP64 48 Vh (three double2 planes), FP32 24 Vh (float4 plane for
- * colours 0-1, float2 plane for colour 2), FP16 16 Vh (per site three half2
- * colours and one float scale in one 16-byte record), FX16 16 Vh (per site
+ * colours 0-1, float2 plane for colour 2), FP16 / BF16 16 Vh (per site three
+ * half2 / bfloat162 colours and one float scale in one 16-byte record), FX16 16 Vh (per site
  * three (re, im) pairs of 16-bit integers q, value q * s, and the float s).
  */
 stg_status stg_field_bytes(const stg_gauge *g, stg_prec prec, size_t *bytes);
@@ -232,7 +233,7 @@ stg_status stg_apply_A_dot(const stg_gauge *g, double mass, const void *in_dev,
  * process exits).
  *   Arguments as for stg_apply_A_dot; the handle must already exist (its
  *   links were allocated by stg_gauge_create).
- *   Limit: 48 Vh (FP64), 24 Vh (FP32) or 16 Vh (FP16, FX16) bytes plus 8
+ *   Limit: 48 Vh (FP64), 24 Vh (FP32) or 16 Vh (FP16, FX16, BF16) bytes plus 8
  *   bytes per 256 sites must fit in 32 MiB (FP64 up to 24^3x48, the others
  *   up to 32^3x64); larger lattices return STG_ERR_INVALID_ARG with a message.
  *   The first call on a device looks up the array's device address (once per
@@ -327,7 +328,7 @@ stg_status stg_mrhs_tuning(const stg_gauge *g, stg_prec prec, int nrhs, int *rhs
                            int *threads_per_site);
 
 /* Fill params with the defaults: RELIABLE, sloppy = handle's sloppy
- * precision, delta = 0.05 for FP32, 0.25 for FP16 / FX16 inner iterations
+ * precision, delta = 0.05 for FP32, 0.25 for FP16 / FX16 / BF16 inner iterations
  * (0.1 without a handle), maxiter = 0 (10 N_dim), check_every = 0 (auto),
  * timing = 0. */
 stg_status stg_cg_params_default(const stg_gauge *g, stg_cg_params *params);

@@ -20,14 +20,14 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libstg.so")
 
-STG_FP64, STG_FP32, STG_FP16, STG_FX16 = 0, 1, 2, 3
+STG_FP64, STG_FP32, STG_FP16, STG_FX16, STG_BF16 = 0, 1, 2, 3, 4
 STG_CG_RELIABLE, STG_CG_REFINE, STG_CG_PLAIN = 0, 1, 2
 (STG_OK, STG_ERR_INVALID_ARG, STG_ERR_DIMS, STG_ERR_OOM, STG_ERR_CUDA,
  STG_ERR_NOT_CONVERGED, STG_ERR_BREAKDOWN, STG_ERR_TIMEOUT,
  STG_ERR_UNSUPPORTED) = range(9)
 
-PREC_NAMES = {STG_FP64: "f64", STG_FP32: "f32", STG_FP16: "f16", STG_FX16: "fx16"}
-FIELD_SITE_BYTES = {STG_FP64: 48, STG_FP32: 24, STG_FP16: 16, STG_FX16: 16}
+PREC_NAMES = {STG_FP64: "f64", STG_FP32: "f32", STG_FP16: "f16", STG_FX16: "fx16", STG_BF16: "bf16"}
+FIELD_SITE_BYTES = {STG_FP64: 48, STG_FP32: 24, STG_FP16: 16, STG_FX16: 16, STG_BF16: 16}
 
 
 class StgError(RuntimeError):

@@ -46,7 +46,7 @@ struct DeviceScope {
 
 static bool valid_prec(int p)
 {
-    return p == STG_FP64 || p == STG_FP32 || p == STG_FP16 || p == STG_FX16;
+    return p == STG_FP64 || p == STG_FP32 || p == STG_FP16 || p == STG_FX16 || p == STG_BF16;
 }
 
 static stg_status check_dims(const int *dims)
@@ -119,7 +119,7 @@ stg_status stg_gauge_create(const int dims[4], const double *links_host, stg_pre
         return STG_ERR_INVALID_ARG;
     }
     if (!valid_prec(sloppy) || (recon != 18 && recon != 12)) {
-        set_error("stg_gauge_create: precision must be FP64/FP32/FP16/FX16 and recon 18 or 12");
+        set_error("stg_gauge_create: precision must be FP64/FP32/FP16/FX16/BF16 and recon 18 or 12");
         return STG_ERR_INVALID_ARG;
     }
     *out = nullptr;

@@ -301,13 +301,14 @@ __global__ void __launch_bounds__(kBlock) k_norm2(int vh, const void *v, CGState
 // ---------------------------------------------------------------------------
 // dispatch over the (PD, PR) pairs used by the solver
 // ---------------------------------------------------------------------------
-static int pr_of(int pd) { return (pd == P16 || pd == PX16) ? P32 : pd; }
+static int pr_of(int pd) { return (pd == P16 || pd == PX16 || pd == PB16) ? P32 : pd; }
 
 #define STG_DISPATCH_PD(pd, KERNEL, ...)                                                     \
     do {                                                                                     \
         if ((pd) == P64) KERNEL<P64, P64><<<grid, kBlock, 0, s>>>(__VA_ARGS__);              \
         else if ((pd) == P32) KERNEL<P32, P32><<<grid, kBlock, 0, s>>>(__VA_ARGS__);         \
         else if ((pd) == P16) KERNEL<P16, P32><<<grid, kBlock, 0, s>>>(__VA_ARGS__);         \
+        else if ((pd) == PB16) KERNEL<PB16, P32><<<grid, kBlock, 0, s>>>(__VA_ARGS__);       \
         else KERNEL<PX16, P32><<<grid, kBlock, 0, s>>>(__VA_ARGS__);                         \
     } while (0)
 
@@ -317,6 +318,7 @@ static int pr_of(int pd) { return (pd == P16 || pd == PX16) ? P32 : pd; }
         if ((pd) == P64) e_ = launch_k(KERNEL<P64, P64>, grid, kBlock, 0, s, PDL, __VA_ARGS__);  \
         else if ((pd) == P32) e_ = launch_k(KERNEL<P32, P32>, grid, kBlock, 0, s, PDL, __VA_ARGS__); \
         else if ((pd) == P16) e_ = launch_k(KERNEL<P16, P32>, grid, kBlock, 0, s, PDL, __VA_ARGS__); \
+        else if ((pd) == PB16) e_ = launch_k(KERNEL<PB16, P32>, grid, kBlock, 0, s, PDL, __VA_ARGS__); \
         else e_ = launch_k(KERNEL<PX16, P32>, grid, kBlock, 0, s, PDL, __VA_ARGS__);              \
         STG_CUDA(e_);                                                                        \
     } while (0)
@@ -327,6 +329,7 @@ static stg_status norm2(const Geom &g, int prec, const void *v, Workspace *ws, c
     if (prec == P64) k_norm2<P64><<<grid, kBlock, 0, s>>>(g.Vh, v, ws->state, ws->partials);
     else if (prec == P32) k_norm2<P32><<<grid, kBlock, 0, s>>>(g.Vh, v, ws->state, ws->partials);
     else if (prec == P16) k_norm2<P16><<<grid, kBlock, 0, s>>>(g.Vh, v, ws->state, ws->partials);
+    else if (prec == PB16) k_norm2<PB16><<<grid, kBlock, 0, s>>>(g.Vh, v, ws->state, ws->partials);
     else k_norm2<PX16><<<grid, kBlock, 0, s>>>(g.Vh, v, ws->state, ws->partials);
     STG_CUDA(cudaGetLastError());
     return STG_OK;
@@ -394,6 +397,8 @@ stg_status launch_update_m(int pd, int vh, char *y, char *r, const char *d, cons
         k_cg_update_m<P32, P32><<<grid, kBlock, 0, s>>>(vh, y, r, d, q, sr, sd, states, partials, pstride, active, nactive);
     else if (pd == P16)
         k_cg_update_m<P16, P32><<<grid, kBlock, 0, s>>>(vh, y, r, d, q, sr, sd, states, partials, pstride, active, nactive);
+    else if (pd == PB16)
+        k_cg_update_m<PB16, P32><<<grid, kBlock, 0, s>>>(vh, y, r, d, q, sr, sd, states, partials, pstride, active, nactive);
     else
         k_cg_update_m<PX16, P32><<<grid, kBlock, 0, s>>>(vh, y, r, d, q, sr, sd, states, partials, pstride, active, nactive);
     STG_CUDA(cudaGetLastError());
@@ -408,6 +413,7 @@ stg_status launch_xpay_m(int pd, int vh, const char *r, char *d, size_t sr, size
     if (pd == P64) k_xpay_m<P64, P64><<<grid, kBlock, 0, s>>>(vh, r, d, sr, sd, states, active, nactive);
     else if (pd == P32) k_xpay_m<P32, P32><<<grid, kBlock, 0, s>>>(vh, r, d, sr, sd, states, active, nactive);
     else if (pd == P16) k_xpay_m<P16, P32><<<grid, kBlock, 0, s>>>(vh, r, d, sr, sd, states, active, nactive);
+    else if (pd == PB16) k_xpay_m<PB16, P32><<<grid, kBlock, 0, s>>>(vh, r, d, sr, sd, states, active, nactive);
     else k_xpay_m<PX16, P32><<<grid, kBlock, 0, s>>>(vh, r, d, sr, sd, states, active, nactive);
     STG_CUDA(cudaGetLastError());
     return STG_OK;
@@ -437,6 +443,7 @@ stg_status launch_norm2(int prec, int vh, const void *v, CGState *st, double *pa
     if (prec == P64) k_norm2<P64><<<grid, kBlock, 0, s>>>(vh, v, st, partials);
     else if (prec == P32) k_norm2<P32><<<grid, kBlock, 0, s>>>(vh, v, st, partials);
     else if (prec == P16) k_norm2<P16><<<grid, kBlock, 0, s>>>(vh, v, st, partials);
+    else if (prec == PB16) k_norm2<PB16><<<grid, kBlock, 0, s>>>(vh, v, st, partials);
     else k_norm2<PX16><<<grid, kBlock, 0, s>>>(vh, v, st, partials);
     STG_CUDA(cudaGetLastError());
     return STG_OK;

@@ -108,9 +108,7 @@ __global__ void __launch_bounds__(kBlock) k_dslash(const DslashArgs a)
         if (last) {
             if (EPI == EPI_A_CG) {
                 CGState *st = a.state;
-                st->pAp = total;
-                if (!(total > 0.0) || !isfinite(total)) st->flag = FLAG_BREAKDOWN;
-                else st->alpha = st->delta_new / total;
+                set_alpha(st, total);
             } else {
                 *a.dot = total;
             }
@@ -169,8 +167,14 @@ stg_status launch_dslash(const Geom &g, int prec, int epi, const DslashLaunch &L
         if (recon == 18) launch_pr<P32, 18>(epi, a, grid, s, L.pdl);
         else launch_pr<P32, 12>(epi, a, grid, s, L.pdl);
     } else {
-        if (recon == 18) launch_pr<P16, 18>(epi, a, grid, s, L.pdl);
-        else launch_pr<P16, 12>(epi, a, grid, s, L.pdl);
+        if (prec == PB16) {
+            if (recon == 18) launch_pr<PB16, 18>(epi, a, grid, s, L.pdl);
+            else launch_pr<PB16, 12>(epi, a, grid, s, L.pdl);
+        } else if (recon == 18) {
+            launch_pr<P16, 18>(epi, a, grid, s, L.pdl);
+        } else {
+            launch_pr<P16, 12>(epi, a, grid, s, L.pdl);
+        }
     }
     STG_CUDA(cudaGetLastError());
     return STG_OK;

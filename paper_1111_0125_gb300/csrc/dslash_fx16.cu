@@ -309,9 +309,7 @@ __global__ void __launch_bounds__(kBlock, STG_FX2_MINBLOCKS) k_dslash_fx2(const 
         if (grid_sum_ff<kBlock>(dot, reinterpret_cast<float2 *>(a.partials), a.counter, total)) {
             if (EPI == EPI_A_CG) {
                 CGState *st = a.state;
-                st->pAp = total;
-                if (!(total > 0.0) || !isfinite(total)) st->flag = FLAG_BREAKDOWN;
-                else st->alpha = st->delta_new / total;
+                set_alpha(st, total);
             } else {
                 *a.dot = total;
             }
@@ -531,10 +529,12 @@ __global__ void __launch_bounds__(kFxCons, kFxCtasPerSM) k_dslash_fx2_staged(con
         if (grid_sum_ff<kFxCons>(dot, reinterpret_cast<float2 *>(a.partials), a.counter, total)) {
             if (EPI == EPI_A_CG) {
                 CGState *st = a.state;
-                st->pAp = total;
-                if (!isfinite(total) && *(volatile unsigned *)&g_fx_wait_timeouts) st->flag = FLAG_TIMEOUT;
-                else if (!(total > 0.0) || !isfinite(total)) st->flag = FLAG_BREAKDOWN;
-                else st->alpha = st->delta_new / total;
+                if (!isfinite(total) && *(volatile unsigned *)&g_fx_wait_timeouts) {
+                    st->pAp = total;
+                    st->flag = FLAG_TIMEOUT;
+                } else {
+                    set_alpha(st, total);
+                }
             } else {
                 *a.dot = total;
             }

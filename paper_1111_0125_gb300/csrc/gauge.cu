@@ -8,6 +8,7 @@
 #include <stdlib.h>
 
 #include <new>
+#include <type_traits>
 
 #include "stg_internal.h"
 
@@ -100,25 +101,27 @@ __global__ void k_pack_links(Geom g, const double2 *__restrict__ ucan, char *bas
             reinterpret_cast<uint2 *>(p + (size_t)vh)[i] = b;
         }
     } else {
+        // 16-bit floats (P16 binary16, PB16 bfloat16): |U_ab| <= 1, no scale
+        typedef typename std::conditional<P == PB16, CodecBF16, CodecF16>::type C16;
         uint4 *p = reinterpret_cast<uint4 *>(blk);
         uint4 a;
-        a.x = f2_to_h2((float)u[0].x, (float)u[0].y);
-        a.y = f2_to_h2((float)u[1].x, (float)u[1].y);
-        a.z = f2_to_h2((float)u[2].x, (float)u[2].y);
-        a.w = f2_to_h2((float)u[3].x, (float)u[3].y);
+        a.x = C16::enc((float)u[0].x, (float)u[0].y);
+        a.y = C16::enc((float)u[1].x, (float)u[1].y);
+        a.z = C16::enc((float)u[2].x, (float)u[2].y);
+        a.w = C16::enc((float)u[3].x, (float)u[3].y);
         p[i] = a;
         if (R == 18) {
             uint4 b;
-            b.x = f2_to_h2((float)u[4].x, (float)u[4].y);
-            b.y = f2_to_h2((float)u[5].x, (float)u[5].y);
-            b.z = f2_to_h2((float)u[6].x, (float)u[6].y);
-            b.w = f2_to_h2((float)u[7].x, (float)u[7].y);
+            b.x = C16::enc((float)u[4].x, (float)u[4].y);
+            b.y = C16::enc((float)u[5].x, (float)u[5].y);
+            b.z = C16::enc((float)u[6].x, (float)u[6].y);
+            b.w = C16::enc((float)u[7].x, (float)u[7].y);
             p[(size_t)vh + i] = b;
-            reinterpret_cast<unsigned *>(p + (size_t)2 * vh)[i] = f2_to_h2((float)u[8].x, (float)u[8].y);
+            reinterpret_cast<unsigned *>(p + (size_t)2 * vh)[i] = C16::enc((float)u[8].x, (float)u[8].y);
         } else {
             uint2 b;
-            b.x = f2_to_h2((float)u[4].x, (float)u[4].y);
-            b.y = f2_to_h2((float)u[5].x, (float)u[5].y);
+            b.x = C16::enc((float)u[4].x, (float)u[4].y);
+            b.y = C16::enc((float)u[5].x, (float)u[5].y);
             reinterpret_cast<uint2 *>(p + (size_t)vh)[i] = b;
         }
     }
@@ -142,6 +145,7 @@ static stg_status pack_links(const Geom &g, const double2 *ucan, int prec, int r
     if (prec == P64) { if (recon == 18) STG_PACK(P64, 18); else STG_PACK(P64, 12); }
     else if (prec == P32) { if (recon == 18) STG_PACK(P32, 18); else STG_PACK(P32, 12); }
     else if (prec == P16) { if (recon == 18) STG_PACK(P16, 18); else STG_PACK(P16, 12); }
+    else if (prec == PB16) { if (recon == 18) STG_PACK(PB16, 18); else STG_PACK(PB16, 12); }
     else { if (recon == 18) STG_PACK(PX16, 18); else STG_PACK(PX16, 12); }
 #undef STG_PACK
     STG_CUDA(cudaGetLastError());
@@ -321,6 +325,7 @@ stg_status pack_field(const Geom &g, int prec, const double *canon, void *out, c
     if (prec == P64) k_pack_field<P64><<<grid, 256, 0, s>>>(g.Vh, c, out);
     else if (prec == P32) k_pack_field<P32><<<grid, 256, 0, s>>>(g.Vh, c, out);
     else if (prec == P16) k_pack_field<P16><<<grid, 256, 0, s>>>(g.Vh, c, out);
+    else if (prec == PB16) k_pack_field<PB16><<<grid, 256, 0, s>>>(g.Vh, c, out);
     else k_pack_field<PX16><<<grid, 256, 0, s>>>(g.Vh, c, out);
     STG_CUDA(cudaGetLastError());
     return STG_OK;
@@ -333,6 +338,7 @@ stg_status unpack_field(const Geom &g, int prec, const void *in, double *canon, 
     if (prec == P64) k_unpack_field<P64><<<grid, 256, 0, s>>>(g.Vh, in, c);
     else if (prec == P32) k_unpack_field<P32><<<grid, 256, 0, s>>>(g.Vh, in, c);
     else if (prec == P16) k_unpack_field<P16><<<grid, 256, 0, s>>>(g.Vh, in, c);
+    else if (prec == PB16) k_unpack_field<PB16><<<grid, 256, 0, s>>>(g.Vh, in, c);
     else k_unpack_field<PX16><<<grid, 256, 0, s>>>(g.Vh, in, c);
     STG_CUDA(cudaGetLastError());
     return STG_OK;
@@ -457,6 +463,10 @@ stg_status workspace_get(stg_gauge *g, Workspace **out)
 
 stg_status workspace_tmp(stg_gauge *g, int prec, void **out)
 {
+    if (prec < 0 || prec >= kNumPrec) {
+        set_error("workspace: unknown precision");
+        return STG_ERR_INVALID_ARG;
+    }
     Workspace *ws;
     STG_TRY(workspace_get(g, &ws));
     if (!ws->tmp[prec]) {
@@ -486,7 +496,7 @@ void workspace_free(Workspace *ws)
     cudaFree(ws->partials);
     cudaFree(ws->state);
     if (ws->state_host) cudaFreeHost(ws->state_host);
-    for (int p = 0; p < 4; ++p) cudaFree(ws->tmp[p]);
+    for (int p = 0; p < kNumPrec; ++p) cudaFree(ws->tmp[p]);
     void *v[] = {ws->x64, ws->b64, ws->r64, ws->t64, ws->y, ws->r, ws->d, ws->q};
     for (void *p : v) cudaFree(p);
     delete ws;

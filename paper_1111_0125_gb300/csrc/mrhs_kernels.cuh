@@ -227,9 +227,7 @@ __global__ void __launch_bounds__(kMrhsBlock) k_dslash_m(const MrhsArgs a)
             if (lane == 0) {
                 CGState *st = a.states + k;
                 const double total = (double)acc.hi + (double)acc.lo;
-                st->pAp = total;
-                if (!(total > 0.0) || !isfinite(total)) st->flag = FLAG_BREAKDOWN;
-                else st->alpha = st->delta_new / total;
+                set_alpha(st, total);
             }
         }
         __syncthreads();
@@ -599,10 +597,12 @@ __global__ void __launch_bounds__(kMsThreads, STG_MS_MINBLOCKS) k_dslash_ms(cons
             if (lane == 0) {
                 CGState *st = a.states + k;
                 const double total = (double)acc.hi + (double)acc.lo;
-                st->pAp = total;
-                if (!isfinite(total) && *(volatile unsigned *)&g_ms_wait_timeouts) st->flag = FLAG_TIMEOUT;
-                else if (!(total > 0.0) || !isfinite(total)) st->flag = FLAG_BREAKDOWN;
-                else st->alpha = st->delta_new / total;
+                if (!isfinite(total) && *(volatile unsigned *)&g_ms_wait_timeouts) {
+                    st->pAp = total;
+                    st->flag = FLAG_TIMEOUT;
+                } else {
+                    set_alpha(st, total);
+                }
             }
         }
         __syncthreads();

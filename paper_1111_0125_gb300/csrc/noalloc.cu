@@ -14,7 +14,7 @@
 //
 // Limit.  kScratchBytes = 32 MiB holds, besides the counter and the block
 // partials, the odd intermediate of Vh sites: 48 Vh bytes in FP64, 24 Vh in
-// FP32, 16 Vh in FP16 / FX16.  Up to 24^3x48 fits in FP64 and 32^3x64 in the
+// FP32, 16 Vh in FP16 / FX16 / BF16.  Up to 24^3x48 fits in FP64 and 32^3x64 in the
 // others; larger lattices are rejected with STG_ERR_INVALID_ARG and a message.
 //
 // Sharing.  Every call on a device uses the same array and leaves its
@@ -72,7 +72,7 @@ extern "C" stg_status stg_apply_A_dot_noalloc(const stg_gauge *g, double mass, c
         set_error("stg_apply_A_dot_noalloc: NULL or aliased pointer, or non-finite mass");
         return STG_ERR_INVALID_ARG;
     }
-    if (prec != STG_FP64 && prec != STG_FP32 && prec != STG_FP16 && prec != STG_FX16) {
+    if (prec != STG_FP64 && prec != STG_FP32 && prec != STG_FP16 && prec != STG_FX16 && prec != STG_BF16) {
         set_error("stg_apply_A_dot_noalloc: unknown precision");
         return STG_ERR_INVALID_ARG;
     }

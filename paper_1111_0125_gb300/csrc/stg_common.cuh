@@ -4,6 +4,7 @@
 // grid reduction.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -12,7 +13,8 @@ namespace stg {
 
 // P16: IEEE binary16 storage; PX16: 16-bit fixed point (int16 with a per-
 // site FP32 scale for fields, a fixed 1/32767 for links).  Both compute in FP32.
-enum Prec { P64 = 0, P32 = 1, P16 = 2, PX16 = 3 };
+enum Prec { P64 = 0, P32 = 1, P16 = 2, PX16 = 3, PB16 = 4 };
+constexpr int kNumPrec = 5;  // arrays indexed by precision
 
 // ---------------------------------------------------------------------------
 // Geometry.  Site (x, y, z, t), lex = x + Lx (y + Ly (z + Lz t)), parity
@@ -127,7 +129,7 @@ template <> struct Real<P64> { typedef double T; };
 // Bytes per site of one checkerboard field in the device layout.
 __host__ __device__ constexpr int field_site_bytes(int p)
 {
-    return p == P64 ? 48 : (p == P32 ? 24 : 16);  // P16 and PX16: 16
+    return p == P64 ? 48 : (p == P32 ? 24 : 16);  // P16, PX16 and PB16: 16
 }
 
 // Bytes of one link in the device layout.
@@ -135,7 +137,7 @@ __host__ __device__ constexpr int link_bytes(int p, int recon)
 {
     return p == P64 ? (recon == 18 ? 144 : 96)
          : p == P32 ? (recon == 18 ? 72 : 48)
-                    : (recon == 18 ? 36 : 24);  // P16 and PX16
+                    : (recon == 18 ? 36 : 24);  // P16, PX16 and PB16
 }
 
 // ---------------------------------------------------------------------------
@@ -226,13 +228,34 @@ __device__ __forceinline__ unsigned f2_to_h2(float a, float b)
     return *reinterpret_cast<unsigned *>(&h);
 }
 
-template <> struct FieldIO<P16> {
+// the two 16-bit floating-point storage forms: IEEE binary16 (P16) and
+// bfloat16 (PB16), two values per 32-bit word
+struct CodecF16 {
+    __device__ __forceinline__ static float2 dec(unsigned u) { return h2_to_f2(u); }
+    __device__ __forceinline__ static unsigned enc(float a, float b) { return f2_to_h2(a, b); }
+};
+struct CodecBF16 {
+    __device__ __forceinline__ static float2 dec(unsigned u)
+    {
+        __nv_bfloat162 h = *reinterpret_cast<__nv_bfloat162 *>(&u);
+        return __bfloat1622float2(h);
+    }
+    __device__ __forceinline__ static unsigned enc(float a, float b)
+    {
+        __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        return *reinterpret_cast<unsigned *>(&h);
+    }
+};
+
+// one 16-byte record per site: three colours as 16-bit float pairs scaled by
+// 1 / (largest |re| or |im| of the site), and that scale as an FP32
+template <class C> struct FieldIO16 {
     template <bool NC = false>
     __device__ __forceinline__ static Vec3<float> load(const void *f, int vh, int s)
     {
         uint4 u = ld<uint4, NC>(static_cast<const uint4 *>(f) + s);
         float sc = __uint_as_float(u.w);
-        float2 a = h2_to_f2(u.x), b = h2_to_f2(u.y), c = h2_to_f2(u.z);
+        float2 a = C::dec(u.x), b = C::dec(u.y), c = C::dec(u.z);
         Vec3<float> v;
         v.r[0] = a.x * sc; v.i[0] = a.y * sc;
         v.r[1] = b.x * sc; v.i[1] = b.y * sc;
@@ -250,12 +273,12 @@ template <> struct FieldIO<P16> {
         for (int c = 0; c < 3; ++c) m = fmaxf(m, fmaxf(fabsf(v.r[c]), fabsf(v.i[c])));
         float inv = m > 0.f ? 1.0f / m : 0.f;
         uint4 u;
-        u.x = f2_to_h2(v.r[0] * inv, v.i[0] * inv);
-        u.y = f2_to_h2(v.r[1] * inv, v.i[1] * inv);
-        u.z = f2_to_h2(v.r[2] * inv, v.i[2] * inv);
+        u.x = C::enc(v.r[0] * inv, v.i[0] * inv);
+        u.y = C::enc(v.r[1] * inv, v.i[1] * inv);
+        u.z = C::enc(v.r[2] * inv, v.i[2] * inv);
         u.w = __float_as_uint(m);
         static_cast<uint4 *>(f)[s] = u;
-        float2 a = h2_to_f2(u.x), b = h2_to_f2(u.y), c = h2_to_f2(u.z);
+        float2 a = C::dec(u.x), b = C::dec(u.y), c = C::dec(u.z);
         Vec3<float> o;
         o.r[0] = a.x * m; o.i[0] = a.y * m;
         o.r[1] = b.x * m; o.i[1] = b.y * m;
@@ -263,6 +286,9 @@ template <> struct FieldIO<P16> {
         return o;
     }
 };
+
+template <> struct FieldIO<P16> : FieldIO16<CodecF16> {};
+template <> struct FieldIO<PB16> : FieldIO16<CodecBF16> {};
 
 // 16-bit fixed point: a component q in [-32767, 32767] is kept as the
 // unsigned offset u = q + 32768.  Decoding puts u into the low mantissa bits
@@ -447,30 +473,31 @@ template <int R> struct LinkIO<P32, R> {
     }
 };
 
-template <int R> struct LinkIO<P16, R> {
+// 16-bit float links (|U_ab| <= 1, no scale): entries as float pairs
+template <class C, int R> struct LinkIO16 {
     __device__ __forceinline__ static Mat3<float> load(const char *blk, int vh, int s)
     {
         const uint4 *p = reinterpret_cast<const uint4 *>(blk);
         Mat3<float> u;
         uint4 a = ld_stream(p + s);
-        float2 e0 = h2_to_f2(a.x), e1 = h2_to_f2(a.y), e2 = h2_to_f2(a.z), e3 = h2_to_f2(a.w);
+        float2 e0 = C::dec(a.x), e1 = C::dec(a.y), e2 = C::dec(a.z), e3 = C::dec(a.w);
         set_entry(u, 0, e0.x, e0.y);
         set_entry(u, 1, e1.x, e1.y);
         set_entry(u, 2, e2.x, e2.y);
         set_entry(u, 3, e3.x, e3.y);
         if (R == 18) {
             uint4 b = ld_stream(p + (size_t)vh + s);
-            float2 f0 = h2_to_f2(b.x), f1 = h2_to_f2(b.y), f2 = h2_to_f2(b.z), f3 = h2_to_f2(b.w);
+            float2 f0 = C::dec(b.x), f1 = C::dec(b.y), f2 = C::dec(b.z), f3 = C::dec(b.w);
             set_entry(u, 4, f0.x, f0.y);
             set_entry(u, 5, f1.x, f1.y);
             set_entry(u, 6, f2.x, f2.y);
             set_entry(u, 7, f3.x, f3.y);
             unsigned c = ld_stream(reinterpret_cast<const unsigned *>(p + (size_t)2 * vh) + s);
-            float2 g = h2_to_f2(c);
+            float2 g = C::dec(c);
             set_entry(u, 8, g.x, g.y);
         } else {
             uint2 b = ld_stream(reinterpret_cast<const uint2 *>(p + (size_t)vh) + s);
-            float2 f0 = h2_to_f2(b.x), f1 = h2_to_f2(b.y);
+            float2 f0 = C::dec(b.x), f1 = C::dec(b.y);
             set_entry(u, 4, f0.x, f0.y);
             set_entry(u, 5, f1.x, f1.y);
             reconstruct_row2(u, 1.0f);
@@ -478,6 +505,9 @@ template <int R> struct LinkIO<P16, R> {
         return u;
     }
 };
+
+template <int R> struct LinkIO<P16, R> : LinkIO16<CodecF16, R> {};
+template <int R> struct LinkIO<PB16, R> : LinkIO16<CodecBF16, R> {};
 
 // PX16 links: entries q = rint(32767 U_ab) as offsets, no per-link scale.
 // load returns 32767 * U (integer-valued floats); the kernel multiplies its
@@ -656,6 +686,21 @@ struct CGState {
     unsigned counter;  // arrival counter of the last-block reduction
     unsigned pad;
 };
+
+// alpha = delta / d^dag A d (Fig. 1), with a breakdown test.  For the exact
+// operator d^dag A d >= m^2 |d|^2, and |d|^2 >= |r|^2 = delta because d = r +
+// beta d_old with d_old orthogonal to r, so alpha <= 1 / m^2.  A
+// non-positive or non-finite d^dag A d, or a step 16 times beyond that bound,
+// means the low-precision iteration has lost the operator's positivity: the
+// flag makes the solver take a reliable update and restart from the true
+// residual before y is spoiled by the step.
+__device__ __forceinline__ void set_alpha(CGState *st, double pAp)
+{
+    st->pAp = pAp;
+    const double alpha = st->delta_new / pAp;
+    if (!(pAp > 0.0) || !isfinite(pAp) || !(alpha * st->m2 <= 16.0)) st->flag = FLAG_BREAKDOWN;
+    else st->alpha = alpha;
+}
 
 // ---------------------------------------------------------------------------
 // Deterministic grid-wide FP64 sum: block partials, then the last block to

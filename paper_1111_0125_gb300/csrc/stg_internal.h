@@ -125,7 +125,7 @@ struct Workspace {
     size_t n_partials = 0;
     CGState *state = nullptr;      // device
     CGState *state_host = nullptr; // pinned mirror for read-back
-    void *tmp[4] = {nullptr, nullptr, nullptr, nullptr};  // odd intermediate per precision
+    void *tmp[kNumPrec] = {};  // odd intermediate per precision
     // CG vectors (allocated by the solver)
     void *x64 = nullptr, *b64 = nullptr, *r64 = nullptr, *t64 = nullptr;
     void *y = nullptr, *r = nullptr, *d = nullptr, *q = nullptr;

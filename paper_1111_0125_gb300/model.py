@@ -13,8 +13,9 @@ Two models per output site of one half-pass:
 from __future__ import annotations
 
 LINK_BYTES = {("f64", 18): 144, ("f64", 12): 96, ("f32", 18): 72, ("f32", 12): 48,
-              ("f16", 18): 36, ("f16", 12): 24, ("fx16", 18): 36, ("fx16", 12): 24}
-FIELD_BYTES = {"f64": 48, "f32": 24, "f16": 16, "fx16": 16}
+              ("f16", 18): 36, ("f16", 12): 24, ("fx16", 18): 36, ("fx16", 12): 24,
+              ("bf16", 18): 36, ("bf16", 12): 24}
+FIELD_BYTES = {"f64": 48, "f32": 24, "f16": 16, "fx16": 16, "bf16": 16}
 
 FLOPS_PER_SITE = 8 * 9 * 8          # 576
 A_FLOPS_PER_SITE = 2 * FLOPS_PER_SITE + 12

@@ -21,7 +21,10 @@ from paper_1111_0125_gb300 import Gauge
 
 pytestmark = pytest.mark.gpu
 
-TOL = {stg.STG_FP64: 1e-12, stg.STG_FP32: 1e-6, stg.STG_FP16: 2e-3, stg.STG_FX16: 1e-4}
+# BF16 (8 significand bits, unit round-off 2^-8) misses FP16's 2e-3; its
+# measured error is asserted separately below
+TOL = {stg.STG_FP64: 1e-12, stg.STG_FP32: 1e-6, stg.STG_FP16: 2e-3, stg.STG_FX16: 1e-4,
+       stg.STG_BF16: 1e-2}
 
 # several tiles and ragged tails: Vh = 128, 8, 192, 1440, 2520, 20736
 DIMS = [(4, 4, 4, 4), (2, 2, 2, 2), (4, 6, 2, 8), (6, 4, 10, 12), (10, 6, 6, 14),
@@ -48,7 +51,8 @@ def _cuda():
     torch.cuda.synchronize()
 
 
-@pytest.mark.parametrize("prec", [stg.STG_FP64, stg.STG_FP32, stg.STG_FP16, stg.STG_FX16])
+@pytest.mark.parametrize("prec", [stg.STG_FP64, stg.STG_FP32, stg.STG_FP16, stg.STG_FX16,
+                                  stg.STG_BF16])
 def test_pack_unpack_roundtrip(prec):
     dims = (6, 4, 10, 12)
     U = _links(dims)
@@ -58,14 +62,16 @@ def test_pack_unpack_roundtrip(prec):
     if prec == stg.STG_FP64:
         assert np.array_equal(back, chi)
     else:
-        assert rel(back, chi) < {stg.STG_FP32: 1e-7, stg.STG_FP16: 1e-3, stg.STG_FX16: 5e-5}[prec]
+        assert rel(back, chi) < {stg.STG_FP32: 1e-7, stg.STG_FP16: 1e-3, stg.STG_FX16: 5e-5,
+                                 stg.STG_BF16: 5e-3}[prec]
 
 
 @pytest.mark.parametrize("dims", DIMS)
 @pytest.mark.parametrize("prec,recon", [(stg.STG_FP64, 18), (stg.STG_FP64, 12),
                                         (stg.STG_FP32, 18), (stg.STG_FP32, 12),
                                         (stg.STG_FP16, 18), (stg.STG_FP16, 12),
-                                        (stg.STG_FX16, 18), (stg.STG_FX16, 12)])
+                                        (stg.STG_FX16, 18), (stg.STG_FX16, 12),
+                                        (stg.STG_BF16, 18), (stg.STG_BF16, 12)])
 def test_dslash_matches_oracle(dims, prec, recon):
     U = _links(dims, "haar", seed=sum(dims))
     with Gauge(dims, U, sloppy=prec, recon=recon) as g:
@@ -79,7 +85,7 @@ def test_dslash_matches_oracle(dims, prec, recon):
 @pytest.mark.parametrize("dims", [(4, 4, 4, 4), (6, 4, 10, 12), (12, 12, 12, 24)])
 @pytest.mark.parametrize("prec,recon", [(stg.STG_FP64, 18), (stg.STG_FP32, 18),
                                         (stg.STG_FP32, 12), (stg.STG_FP16, 12),
-                                        (stg.STG_FX16, 12)])
+                                        (stg.STG_FX16, 12), (stg.STG_BF16, 12)])
 def test_apply_A_and_dot_match_oracle(dims, prec, recon):
     U = _links(dims, "exp", seed=3, eps=0.4)
     mass = 0.05
@@ -231,3 +237,41 @@ def test_staged_fx16_tiles_per_cta(monkeypatch, grid):
     finally:
         plain.close()
         staged.close()
+
+
+def test_bf16_error_is_reported_beside_fp16():
+    """BF16 storage: the Dslash error against the oracle, measured on
+    12^3x24 (printed), lies above FP16's (8 against 11 significand bits)
+    and below 1e-2."""
+    dims = (12, 12, 12, 24)
+    U = _links(dims, "exp", seed=7, eps=0.5)
+    chi = gen.source(dims, seed=8)
+    want = oracle.dslash(dims, U, chi, out_parity=1)
+    err = {}
+    for prec in (stg.STG_FP16, stg.STG_BF16):
+        with Gauge(dims, U, sloppy=prec, recon=12) as g:
+            out = g.unpack(g.dslash(g.pack(_to_dev(chi), prec), 1, prec), prec)
+            err[prec] = rel(out.cpu().numpy(), want)
+    print(f"Dslash relative error: FP16 {err[stg.STG_FP16]:.2e}, BF16 {err[stg.STG_BF16]:.2e}")
+    assert err[stg.STG_FP16] < 2e-3 and err[stg.STG_FP16] < err[stg.STG_BF16] < 1e-2
+
+
+@pytest.mark.parametrize("mass", [1.0, 0.05])
+def test_cg_bf16_inner(mass):
+    """BF16 inner iterations.  At m = 1 (condition number ~65) the solve
+    converges to 1e-10.  At light masses the 8-bit significand of the stored
+    vectors (Dslash error 2e-3, times the condition number 25600 at m = 0.05)
+    cannot drive the true residual down -- measured: at m = 0.3 the solver
+    stops at maxiter -- and the solver then returns a breakdown or
+    not-converged status, never a wrong x."""
+    dims, tol = (8, 8, 8, 8), 1e-10
+    U = gen.gauge_field(dims, "exp", seed=11, eps=0.4)
+    b = gen.source(dims, seed=12)
+    with Gauge(dims, U, sloppy=stg.STG_BF16, recon=12) as g:
+        try:
+            x, st = g.cg_solve(_to_dev(b), mass, tol, g.params(maxiter=20000))
+        except stg.StgError as e:
+            assert mass < 1.0 and e.status in (stg.STG_ERR_BREAKDOWN, stg.STG_ERR_NOT_CONVERGED)
+            return
+    _check_solution(dims, U, mass, b, x.cpu().numpy(), tol)
+    assert st["sloppy_iters"] == st["iters"] > 0
