@@ -189,7 +189,7 @@ def dslash_bytes(vh, prec, recon, extra_fields):
 # ---------------------------------------------------------------------------
 # CPU oracle (baseline and reference arm)
 # ---------------------------------------------------------------------------
-def oracle_sample(dims, U, mass, b, fp64_iters, budget_s):
+def oracle_sample(dims, U, mass, b, fp64_iters, budget_s, one_thread_s=0.0):
     """Time the FP64 oracle CG (as it stands) for a bounded number of
     iterations on the full lattice and scale to a complete solve."""
     import oracle
@@ -204,10 +204,31 @@ def oracle_sample(dims, U, mass, b, fp64_iters, budget_s):
     per_iter = (tn - t1) / (n - 1)
     solve_s = per_iter * fp64_iters + (t1 - per_iter)
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": 1.0 / solve_s, "unit": "solves/s", "cores": cores, "kind": "oracle",
-            "sample": f"{n} FP64 CG iterations of the oracle on the full {dims} lattice "
-                      f"({tn:.1f} s), scaled to {fp64_iters} iterations (the GPU FP64 CG count)",
-            "seconds_per_solve": solve_s}
+    out = {"value": 1.0 / solve_s, "unit": "solves/s", "cores": cores, "kind": "oracle",
+           "sample": f"{n} FP64 CG iterations of the oracle on the full {dims} lattice "
+                     f"({tn:.1f} s), scaled to {fp64_iters} iterations (the GPU FP64 CG count)",
+           "seconds_per_solve": solve_s}
+    if one_thread_s > 0:
+        # the same oracle on one core (OpenMP runtime of the oracle library)
+        import ctypes
+        try:
+            gomp = ctypes.CDLL("libgomp.so.1")
+        except OSError:
+            gomp = None
+        if gomp is not None:
+            gomp.omp_set_num_threads(1)
+            try:
+                m = max(2, min(50, int(one_thread_s / max(per_iter * cores, 1e-6))))
+                t0 = time.perf_counter()
+                oracle.cg(dims, U, mass, b, tol=0.0, maxiter=m, max_restarts=0)
+                t1m = time.perf_counter() - t0
+            finally:
+                gomp.omp_set_num_threads(cores)
+            solve1 = t1m / m * fp64_iters
+            out["value_1_thread"] = 1.0 / solve1
+            out["sample_1_thread"] = (f"{m} FP64 CG iterations on one core ({t1m:.1f} s), scaled "
+                                      f"to {fp64_iters} iterations")
+    return out
 
 
 def gen_inputs(dims, eps, rank):
@@ -613,7 +634,7 @@ def main():
     cpu = None
     if not args.no_cpu and world == 1:
         cpu = oracle_sample(dims, U, args.mass, b_np, fp64["iters"] if fp64 else 2552,
-                            args.cpu_seconds)
+                            args.cpu_seconds, one_thread_s=6.0)
         cpu.pop("seconds_per_solve")
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
