@@ -65,6 +65,9 @@ def parse():
     ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--load", type=float, default=0.7,
                     help="c5: offered rate as a fraction of the measured saturation rate")
+    ap.add_argument("--chunk", type=int, default=16,
+                    help="c5: CG iterations per session step (larger chunks for small "
+                         "lattices measured worse: slots refill later)")
     ap.add_argument("--no-priority", action="store_true",
                     help="c5: every session on a default-priority stream")
     ap.add_argument("--sweep", type=float, nargs="*", default=[0.3, 0.5],
@@ -420,7 +423,7 @@ def run_c5(args):
     sloppy = {"f32": stg.STG_FP32, "fx16": stg.STG_FX16}[args.sloppy]
     eng = ServeEngine(gauges, sources, hbm_budget=120e9, slots=8, max_sessions_per_gauge=2,
                       max_resident=8, sloppy=sloppy, recon=args.recon,
-                      priority_by_size=not args.no_priority)
+                      priority_by_size=not args.no_priority, chunk=args.chunk)
     try:
         eng.run(c5_requests(64, None, seed=7), realtime=False)       # warm-up, tuning
         sat_res = eng.run(c5_requests(args.requests, None), realtime=False)
@@ -459,6 +462,7 @@ def run_c5(args):
                    "mass": "log-uniform [0.005, 0.1]", "tol": "1e-8 or 1e-10",
                    "hbm_budget_gb": 120, "slots_per_session": 8, "sessions_per_gauge": 2,
                    "stream_priority_by_lattice_size": not args.no_priority,
+                   "iterations_per_step": args.chunk,
                    "sloppy_storage": args.sloppy, "offered_rate": rate,
                    "load_vs_saturation": args.load},
         "p50_ms": summ["p50_ms"], "p99_ms": summ["p99_ms"], "mean_ms": summ["mean_ms"],
