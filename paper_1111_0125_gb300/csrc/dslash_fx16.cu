@@ -368,9 +368,10 @@ __global__ void __launch_bounds__(kFxCons, kFxCtasPerSM) k_dslash_fx2_staged(con
     const int vh = a.g.Vh;
     const int ntiles = (vh + kFxTile - 1) / kFxTile;
     const int c = threadIdx.x, lane = c & 31;
-    // Before the wait only the flag's writer two kernels back has completed
-    // (the predecessor triggers after its own wait), so this read only
-    // decides whether to prefetch; the check after the wait decides.
+    // Before the wait only kernels two or more back have completed (the
+    // predecessor triggers after its own wait); the flag's writer is one of
+    // them, except for a timeout, so this read only decides whether to
+    // prefetch and the check after the wait decides.
     const bool prefetch = (EPI != EPI_A_CG && EPI != EPI_GATE) ||
                           *(volatile const int *)&a.state->flag == FLAG_RUN;
     // the (tile, mu) items of this CTA in order, item q = 4 j + mu, go
