@@ -275,3 +275,20 @@ def test_cg_bf16_inner(mass):
             return
     _check_solution(dims, U, mass, b, x.cpu().numpy(), tol)
     assert st["sloppy_iters"] == st["iters"] > 0
+
+
+def test_dependent_launch_changes_no_bit():
+    """The solver's chunks run with programmatic dependent launch; with
+    timing on, chunks rotate through graphs with per-kernel events and with
+    serial launches.  All compute the same thing in the same order, so the
+    solution is bitwise the same either way (no kernel reads its
+    predecessor's output early)."""
+    dims, mass, tol = (16, 16, 16, 32), 0.02, 1e-10
+    U = _links(dims, "exp", seed=21, eps=0.5)
+    b = gen.source(dims, seed=22)
+    with Gauge(dims, U, sloppy=stg.STG_FX16, recon=12) as g:
+        x0, s0 = g.cg_solve(_to_dev(b), mass, tol, g.params(timing=0))
+        x1, s1 = g.cg_solve(_to_dev(b), mass, tol, g.params(timing=1))
+    assert s0["iters"] == s1["iters"] and s0["updates"] == s1["updates"]
+    assert torch.equal(x0, x1)
+    assert s1["t_iter_ms"] > 0 and s1["t_iter_serial_ms"] > 0 and s1["timed_iters"] > 0
