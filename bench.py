@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--load", type=float, default=0.7,
                     help="c5: offered rate as a fraction of the measured saturation rate")
+    ap.add_argument("--slots", type=int, default=4, help="c5: systems per batch session")
+    ap.add_argument("--sessions", type=int, default=2, help="c5: batch sessions per gauge field")
     ap.add_argument("--chunk", type=int, default=16,
                     help="c5: CG iterations per session step (larger chunks for small "
                          "lattices measured worse: slots refill later)")
@@ -421,7 +423,8 @@ def run_c5(args):
         for j in range(4):
             sources[(li, j)] = gen.source(dims, seed=1000 + 10 * li + j)
     sloppy = {"f32": stg.STG_FP32, "fx16": stg.STG_FX16}[args.sloppy]
-    eng = ServeEngine(gauges, sources, hbm_budget=120e9, slots=8, max_sessions_per_gauge=2,
+    eng = ServeEngine(gauges, sources, hbm_budget=120e9, slots=args.slots,
+                      max_sessions_per_gauge=args.sessions,
                       max_resident=8, sloppy=sloppy, recon=args.recon,
                       priority_by_size=not args.no_priority, chunk=args.chunk)
     try:
@@ -460,7 +463,8 @@ def run_c5(args):
                                                            for d, w in C5_LATTICES},
                    "gauge_fields": 8, "sources_per_lattice": 4,
                    "mass": "log-uniform [0.005, 0.1]", "tol": "1e-8 or 1e-10",
-                   "hbm_budget_gb": 120, "slots_per_session": 8, "sessions_per_gauge": 2,
+                   "hbm_budget_gb": 120, "slots_per_session": args.slots,
+                   "sessions_per_gauge": args.sessions,
                    "stream_priority_by_lattice_size": not args.no_priority,
                    "iterations_per_step": args.chunk,
                    "sloppy_storage": args.sloppy, "offered_rate": rate,

@@ -164,7 +164,7 @@ class ServeEngine:
     sources: key -> canonical host source (complex128 [Vh][3]); pinned on entry
     """
 
-    def __init__(self, gauges: dict, sources: dict, hbm_budget: float = 120e9, slots: int = 8,
+    def __init__(self, gauges: dict, sources: dict, hbm_budget: float = 120e9, slots: int = 4,
                  max_sessions_per_gauge: int = 2, max_resident: int = 8, sloppy: int = STG_FP32,
                  recon: int = 12, chunk: int = 16, keep_solutions: bool = False, device: int = 0,
                  priority_by_size: bool = True):
