@@ -604,8 +604,12 @@ def main():
     # t_serial) / 4.  The solver's own chunks use dependent launch: t_iter.
     raw = {k: statistics.mean(s_[f"t_{k}_ms"] for s_ in stats)
            for k in ("dslash", "dslash_a", "update", "xpay")}
-    t_iter = statistics.mean(s_["t_iter_ms"] for s_ in stats)
-    t_serial = statistics.mean(s_["t_iter_serial_ms"] for s_ in stats)
+    def mean_pos(key):
+        v = [s_[key] for s_ in stats if s_[key] > 0]
+        return statistics.mean(v) if v else 0.0
+
+    t_iter = mean_pos("t_iter_ms")
+    t_serial = mean_pos("t_iter_serial_ms")
     gap = max(0.0, (sum(raw.values()) - t_serial) / 4.0) if t_serial > 0 else 0.0
     cal = {k: v - gap for k, v in raw.items()}
     staged = args.sloppy == "fx16" and args.recon == 12

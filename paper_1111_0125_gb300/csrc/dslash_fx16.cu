@@ -473,7 +473,7 @@ __global__ void __launch_bounds__(kFxCons, kFxCtasPerSM) k_dslash_fx2_staged(con
             const uint4 ba = b16[c], bb = b16[c + kFxCons];
             const uint2 bc = b8[c], bd = b8[c + kFxCons];
             // release the stage: the last warp to finish reading it refills
-            // it with this CTA's next tile
+            // it with the item kFxStages further on
             __syncwarp();
             if (lane == 0) {
                 __threadfence_block();
