@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--load", type=float, default=0.7,
                     help="c5: offered rate as a fraction of the measured saturation rate")
     ap.add_argument("--slots", type=int, default=4, help="c5: systems per batch session")
+    ap.add_argument("--rate", type=float, default=0.0,
+                    help="c5: offered rate at --load in requests/s (0: --load x saturation)")
     ap.add_argument("--sessions", type=int, default=2, help="c5: batch sessions per gauge field")
     ap.add_argument("--chunk", type=int, default=16,
                     help="c5: CG iterations per session step (larger chunks for small "
@@ -436,6 +438,8 @@ def run_c5(args):
         sweep = []
         for load in sorted({*args.sweep, args.load}):
             r_ = load * sat["solves_per_s"]
+            if args.rate > 0:   # an absolute offered rate (requests / s) instead
+                r_ = args.rate * load / args.load
             clocks = ClockSampler("")
             res_ = eng.run(c5_requests(args.requests, r_), realtime=True)
             ck_ = clocks.stop()
