@@ -200,3 +200,34 @@ def test_c4_batched_24x48_sixteen_masses():
     for k in range(n):
         r = bs[k] - oracle.apply_A(dims, U, masses[k], xs[k])
         assert np.linalg.norm(r) <= tol * np.linalg.norm(bs[k]), k
+
+
+@pytest.mark.parametrize("shape", [None, "9", "11"])
+def test_mrhs_at_the_system_limit(monkeypatch, shape):
+    """64 systems, the most one call takes: every system's Dslash and A
+    against the oracle (tuned shape, and the staged kernel with NB = 2 and 8,
+    whose per-warp reduction slots run up to system 63), then a batched CG
+    of all 64."""
+    if shape is not None:
+        monkeypatch.setenv("STG_MRHS_SHAPE", shape)
+    dims, n, prec = (4, 4, 4, 8), 64, stg.STG_FP32
+    U = gen.gauge_field(dims, "exp", seed=31, eps=0.5)
+    chis = list(gen.source(dims, seed=32, nrhs=n))
+    masses = gen.log_uniform(n, 0.05, 0.5, seed=33)
+    with stg.Gauge(dims, U, sloppy=prec, recon=12) as g:
+        buf, fb = _pack_batch(g, chis, prec)
+        ins = _unpack_batch(g, buf, fb, n, prec)
+        out = torch.empty_like(buf)
+        stg.stg_dslash_mrhs(g.handle, 0, n, buf, out, prec)
+        got = _unpack_batch(g, out, fb, n, prec)
+        for k in range(n):
+            assert rel(got[k], oracle.dslash(dims, U, ins[k], 0)) < TOL[prec], k
+        stg.stg_apply_A_mrhs(g.handle, n, masses, buf, out, prec)
+        got = _unpack_batch(g, out, fb, n, prec)
+        for k in range(n):
+            assert rel(got[k], oracle.apply_A(dims, U, masses[k], ins[k])) < TOL[prec], k
+        xs, st = _solve_batch(g, chis, masses, 1e-10, prec)
+    for k in range(n):
+        r = chis[k] - oracle.apply_A(dims, U, masses[k], xs[k])
+        assert np.linalg.norm(r) <= 1e-10 * np.linalg.norm(chis[k]), k
+        assert st[k]["true_res"] <= 1e-10
