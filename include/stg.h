@@ -29,7 +29,8 @@
  *     fields: complex128 [Vh][3] over one parity in checkerboard order
  *             (device memory), i.e. 6 doubles (re, im) x 3 colours per site.
  *   Device layouts ("field" arguments below) are the library's structure-of-
- *   arrays forms for FP64 / FP32 / FP16; stg_field_bytes() gives their size
+ *   arrays forms for FP64 / FP32 and per-site records for the 16-bit forms;
+ *   stg_field_bytes() gives their size
  *   and stg_pack_field() / stg_unpack_field() convert.
  *
  *   Ownership.  The caller owns every buffer it passes; the library never
@@ -37,7 +38,9 @@
  *   gauge handle's device copies of the links and a per-handle workspace
  *   (allocated on first use, freed by stg_gauge_destroy).  Calls that use the
  *   same handle must not overlap (one host thread and one stream at a time);
- *   distinct handles are independent.
+ *   distinct handles are independent.  Batch sessions are the exception:
+ *   each owns its workspace, and several sessions on one handle may step
+ *   concurrently on different streams (stg_batch_create).
  *
  *   Streams.  Every call enqueues its GPU work on `stream` (NULL = the legacy
  *   default stream).  stg_dslash, stg_apply_A*, stg_pack_field and
