@@ -206,6 +206,23 @@ stg_status stg_dslash(const stg_gauge *g, int out_parity, const void *in_dev,
                       void *out_dev, stg_prec prec, stg_stream_t stream);
 
 /*
+ * Several lattices in one launch: out_dev[k] = D_{p_k <- 1-p_k} in_dev[k] on
+ * handle g[k] (Eq. 5), k = 0..n-1, n <= 16, p_k = out_parity[k].  The
+ * handles may hold lattices of different sizes but must share the device
+ * and the reconstruction (18 or 12) of their links in `prec`.  Each item's
+ * output is bitwise the one of stg_dslash where that runs the one-site-per-
+ * thread kernel (every precision but FX16 / 12-real, whose stg_dslash runs
+ * the packed staged kernel: agreement to rounding); the group runs as one
+ * grid, which fills the GPU where one small lattice would not.  Arrays are host arrays of n entries; fields as for stg_dslash (no
+ * item's output may alias any item's input).  The paper applies the
+ * operator to one lattice at a time; this is a serving-layer form of it.
+ * Errors: STG_ERR_INVALID_ARG, STG_ERR_UNSUPPORTED, STG_ERR_CUDA.
+ */
+stg_status stg_dslash_group(int n, const stg_gauge *const *g, const int *out_parity,
+                            const void *const *in_dev, void *const *out_dev, stg_prec prec,
+                            stg_stream_t stream);
+
+/*
  * Even-site normal operator (Eq. 3): out = m^2 in - D_eo (D_oe in).
  * in_dev / out_dev: even fields in the device layout of prec (no aliasing).
  * The odd intermediate lives in the handle's workspace.

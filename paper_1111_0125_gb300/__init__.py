@@ -88,6 +88,7 @@ def _load():
         "stg_cg_params_default": (i, [p, p]),
         "stg_cg_solve": (i, [p, p, p, d, d, p, p, p]),
         "stg_dslash_mrhs": (i, [p, i, i, p, p, i, p]),
+        "stg_dslash_group": (i, [i, p, p, p, p, i, p]),
         "stg_apply_A_mrhs": (i, [p, i, p, p, p, i, p]),
         "stg_cg_solve_mrhs": (i, [p, i, p, p, p, d, p, p, p]),
         "stg_mrhs_tuning": (i, [p, i, i, p, p]),
@@ -229,6 +230,18 @@ def stg_cg_solve(handle: int, src_dev, x_dev, mass: float, tol: float, params=No
                           ctypes.byref(stats), _stream(stream))
     _check(st, "stg_cg_solve", stats.as_dict())
     return stats.as_dict()
+
+
+def stg_dslash_group(handles, out_parities, ins, outs, prec: int, stream=None) -> None:
+    """out[k] = D in[k] on handles[k] for up to 16 lattices in one launch."""
+    n = len(handles)
+    if not (len(out_parities) == len(ins) == len(outs) == n):
+        raise ValueError("stg_dslash_group: handles, parities, ins and outs differ in length")
+    hs = (ctypes.c_void_p * n)(*[int(h) for h in handles])
+    ps = (ctypes.c_int * n)(*[int(q) for q in out_parities])
+    xi = (ctypes.c_void_p * n)(*[_ptr(x) for x in ins])
+    xo = (ctypes.c_void_p * n)(*[_ptr(x) for x in outs])
+    _check(lib.stg_dslash_group(n, hs, ps, xi, xo, int(prec), _stream(stream)), "stg_dslash_group")
 
 
 def stg_dslash_mrhs(handle: int, out_parity: int, nrhs: int, in_dev, out_dev, prec: int,

@@ -21,7 +21,7 @@
 //   EPI_A_DOT as EPI_A, plus Re sum w^dag out in FP64 -> *dot
 //   EPI_A_CG  as EPI_A_DOT inside CG: alpha = delta / d^dag A d -> state
 //   EPI_RES   out = w - m^2 v + D in = b - A x, plus |out|^2 in FP64 -> *dot
-#include "stg_internal.h"
+#include "dslash_site.cuh"
 
 namespace stg {
 
@@ -38,32 +38,7 @@ __global__ void __launch_bounds__(kBlock) k_dslash(const DslashArgs a)
     const int vh = a.g.Vh;
     T dot = T(0);
     if (i < vh) {
-        const Site s = site_of(a.g, i, a.parity);
-        Vec3<T> acc;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) acc.r[c] = acc.i[c] = T(0);
-#pragma unroll
-        for (int mu = 0; mu < 4; ++mu) {
-            int jf, jb;
-            neighbours(a.g, s, i, mu, jf, jb);
-            float sf = 1.f, sb = 1.f;
-            if (R == 12) link_signs(a.g, s, mu, sf, sb);
-            const T s2f = (R == 12) ? T(sf * LinkPost<P>::row2) : T(1);
-            const T s2b = (R == 12) ? T(sb * LinkPost<P>::row2) : T(1);
-            const Mat3<T> uf = LinkIO<P, R>::load(a.lf[mu], vh, i);
-            const Vec3<T> vf = FieldIO<P>::load_nc(a.in, vh, jf);
-            mul_add(uf, vf, acc, s2f);
-            const Mat3<T> ub = LinkIO<P, R>::load(a.lb[mu], vh, jb);
-            const Vec3<T> vb = FieldIO<P>::load_nc(a.in, vh, jb);
-            adj_mul_sub(ub, vb, acc, s2b);
-        }
-        if (P == PX16) {
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                acc.r[c] *= T(LinkPost<PX16>::k);
-                acc.i[c] *= T(LinkPost<PX16>::k);
-            }
-        }
+        const Vec3<T> acc = dslash_site<P, R>(a.g, a.lf, a.lb, a.parity, a.in, i);
         if (EPI == EPI_NONE || EPI == EPI_GATE) {
             FieldIO<P>::store(a.out, vh, i, acc);
         } else if (EPI == EPI_RES) {

@@ -292,3 +292,55 @@ def test_dependent_launch_changes_no_bit():
     assert s0["iters"] == s1["iters"] and s0["updates"] == s1["updates"]
     assert torch.equal(x0, x1)
     assert s1["t_iter_ms"] > 0 and s1["t_iter_serial_ms"] > 0 and s1["timed_iters"] > 0
+
+
+@pytest.mark.parametrize("prec,recon", [(stg.STG_FP64, 18), (stg.STG_FP32, 12),
+                                        (stg.STG_FX16, 12), (stg.STG_FP16, 18)])
+def test_dslash_group_of_lattices(prec, recon):
+    """Four lattices of different sizes (2^4 .. 8^4) and parities in one
+    launch: each output within the precision's tolerance of the oracle, and
+    bitwise equal to its own stg_dslash where that runs the same one-site-
+    per-thread arithmetic (FX16 / 12-real runs the packed staged kernel
+    there, so the two agree to rounding)."""
+    specs = [((4, 4, 4, 4), "haar", 0, 0), ((6, 4, 10, 12), "exp", 1, 1),
+             ((8, 8, 8, 8), "exp", 2, 1), ((2, 2, 2, 2), "haar", 3, 0)]
+    gauges, ins, outs, chis, Us = [], [], [], [], []
+    try:
+        for dims, kind, seed, parity in specs:
+            U = _links(dims, kind, seed=seed)
+            g = Gauge(dims, U, sloppy=prec, recon=recon)
+            chi = gen.source(dims, seed=10 + seed)
+            gauges.append(g)
+            Us.append(U)
+            chis.append(chi)
+            ins.append(g.pack(_to_dev(chi), prec))
+            outs.append(g.new_field(prec))
+        stg.stg_dslash_group([g.handle for g in gauges], [sp[3] for sp in specs], ins, outs, prec)
+        for k, (dims, _, _, parity) in enumerate(specs):
+            single = gauges[k].dslash(ins[k], parity, prec)
+            got = gauges[k].unpack(outs[k], prec).cpu().numpy()
+            if prec == stg.STG_FX16 and recon == 12:
+                one = gauges[k].unpack(single, prec).cpu().numpy()
+                assert rel(got, one) < TOL[prec], k
+            else:
+                assert torch.equal(outs[k], single), k
+            want = oracle.dslash(dims, Us[k], gauges[k].unpack(ins[k], prec).cpu().numpy(), parity)
+            assert rel(got, want) < TOL[prec], k
+        with pytest.raises(stg.StgError) as e:
+            stg.stg_dslash_group([], [], [], [], prec)
+        assert e.value.status == stg.STG_ERR_INVALID_ARG
+    finally:
+        for g in gauges:
+            g.close()
+
+
+def test_dslash_group_rejects_mixed_reconstruction():
+    dims = (4, 4, 4, 4)
+    U = _links(dims)
+    with Gauge(dims, U, sloppy=stg.STG_FP32, recon=12) as a, \
+            Gauge(dims, U, sloppy=stg.STG_FP32, recon=18) as b:
+        f = a.pack(_to_dev(gen.source(dims, seed=1)), stg.STG_FP32)
+        o1, o2 = a.new_field(stg.STG_FP32), b.new_field(stg.STG_FP32)
+        with pytest.raises(stg.StgError) as e:
+            stg.stg_dslash_group([a.handle, b.handle], [0, 0], [f, f], [o1, o2], stg.STG_FP32)
+        assert e.value.status == stg.STG_ERR_INVALID_ARG
