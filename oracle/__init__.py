@@ -56,7 +56,9 @@ def _load():
         lib.orc_apply_A.argtypes = [p, p, ctypes.c_double, p, p]
         lib.orc_cg.argtypes = [p, p, ctypes.c_double, p, p, ctypes.c_double,
                                ctypes.c_long, ctypes.c_int, p, p]
-        for f in ("orc_dslash", "orc_dslash_sites", "orc_apply_A", "orc_cg"):
+        lib.orc_cg_mixed.argtypes = [p, p, ctypes.c_double, p, p, ctypes.c_double,
+                                     ctypes.c_double, ctypes.c_long, p, p]
+        for f in ("orc_dslash", "orc_dslash_sites", "orc_apply_A", "orc_cg", "orc_cg_mixed"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -147,3 +149,27 @@ def cg(dims, U, mass: float, b, tol: float = 1e-10, maxiter: int | None = None,
     _raise(st, "cg")
     return x, dict(status=int(st), iters=int(info[0]), restarts=int(info[1]),
                    true_res=float(res[0]))
+
+
+def cg_mixed(dims, U, mass: float, b, tol: float = 1e-10, delta: float = 0.1,
+             maxiter: int | None = None, x0=None):
+    """Mixed-precision CG (Fig. 2, Eq. 6, Sec. 3.2) emulated with single-
+    precision inner vectors and double updates.
+
+    Returns (x, info) with info = dict(status, iters, updates, true_res,
+    low_precision_fraction = iters / (iters + updates)).
+    """
+    lib = _load()
+    dd, U, b = _dims(dims), _c128(U), _c128(b)
+    _check_shapes(dims, U, b)
+    x = np.zeros_like(b) if x0 is None else _c128(x0).copy()
+    if maxiter is None:
+        maxiter = 10 * 3 * _vh(dims)
+    info = np.zeros(2, dtype=np.int64)
+    res = np.zeros(1, dtype=np.float64)
+    st = lib.orc_cg_mixed(_ptr(dd), _ptr(U), float(mass), _ptr(b), _ptr(x), float(tol),
+                          float(delta), int(maxiter), _ptr(info), _ptr(res))
+    _raise(st, "cg_mixed")
+    it, up = int(info[0]), int(info[1])
+    return x, dict(status=int(st), iters=it, updates=up, true_res=float(res[0]),
+                   low_precision_fraction=it / max(1, it + up))

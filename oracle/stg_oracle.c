@@ -251,4 +251,111 @@ done:
     return status;
 }
 
+/*
+ * Mixed-precision CG emulated on the CPU (Fig. 2 with the corrected inner
+ * start of Eq. 6 and the reliable / group-wise updates of Sec. 3.2), for the
+ * iteration behaviour of the method; not a bitwise model of the GPU (its
+ * rounding order differs).  The inner vectors y, r^, d and q are stored in
+ * single precision (float complex); A is applied in double to the single-
+ * precision d and its result rounded to single; inner products are summed
+ * in double.  x, b, the true residual b - A x and the updates are double.
+ *
+ * Trigger (Sec. 3.2, reading of "Max(|r^y|)"): |r^|^2 < delta_in^2 times the
+ * largest |r^|^2 since the last update, or |r^|^2 <= tol^2 |b|^2.  At a
+ * trigger: x += y, r = b - A x (double), y = 0, r^ = r (group-wise update);
+ * if |r| <= tol |b| the solve ends; else d = r^ + beta d with beta =
+ * |r|^2 / (the iterated |r^|^2 before the triggering step) (Eq. 6, d kept).
+ *
+ * info[0] = inner iterations, info[1] = updates; res[0] = |b - A x| / |b|.
+ * Returns ORC_OK, ORC_NOT_CONVERGED or ORC_BREAKDOWN (d^dag A d <= 0).
+ */
+typedef float complex fcplx;
+
+int orc_cg_mixed(const int *L, const cplx *U, double mass, const cplx *b, cplx *x,
+                 double tol, double delta_in, long maxiter, long *info, double *res)
+{
+    int e = check_dims(L);
+    if (e) return e;
+    if (!U || !b || !x || !info || !res || tol < 0.0 || maxiter < 0 ||
+        !(delta_in > 0.0 && delta_in < 1.0))
+        return ORC_ERR_ARG;
+    long n = volume(L) / 2 * 3;
+    cplx *rt = (cplx *)malloc(sizeof(cplx) * n);    /* true residual (double) */
+    cplx *ad = (cplx *)malloc(sizeof(cplx) * n);    /* A applied in double */
+    cplx *wk = (cplx *)malloc(sizeof(cplx) * n);    /* odd intermediate */
+    fcplx *ys = (fcplx *)malloc(sizeof(fcplx) * n); /* single-precision vectors */
+    fcplx *rs = (fcplx *)malloc(sizeof(fcplx) * n);
+    fcplx *ds = (fcplx *)malloc(sizeof(fcplx) * n);
+    fcplx *qs = (fcplx *)malloc(sizeof(fcplx) * n);
+    if (!rt || !ad || !wk || !ys || !rs || !ds || !qs) {
+        free(rt); free(ad); free(wk); free(ys); free(rs); free(ds); free(qs);
+        return ORC_ERR_OOM;
+    }
+    double b2 = re_dot(b, b, n), goal = tol * tol * b2;
+    long it = 0, ups = 0;
+    int status = ORC_NOT_CONVERGED;
+
+    /* true residual of the start */
+    apply_A_tmp(L, U, mass, x, ad, wk);
+    for (long k = 0; k < n; ++k) rt[k] = b[k] - ad[k];
+    double true2 = re_dot(rt, rt, n);
+    if (b2 == 0.0 || true2 <= goal) { status = ORC_OK; goto out; }
+
+    /* inner start: y = 0, r^ = r, d = r^ */
+    double rho = 0.0;
+    for (long k = 0; k < n; ++k) {
+        ys[k] = 0.0f;
+        rs[k] = (fcplx)rt[k];
+        ds[k] = rs[k];
+        rho += creal(conj((cplx)rs[k]) * (cplx)rs[k]);
+    }
+    double rho_max = rho;
+    while (it < maxiter) {
+        for (long k = 0; k < n; ++k) wk[k] = (cplx)ds[k];
+        apply_A_tmp(L, U, mass, wk, ad, rt);   /* rt serves as the odd scratch here */
+        double dAd = 0.0;
+        for (long k = 0; k < n; ++k) {
+            qs[k] = (fcplx)ad[k];
+            dAd += creal(conj((cplx)ds[k]) * (cplx)qs[k]);
+        }
+        if (!(dAd > 0.0)) { status = ORC_BREAKDOWN; break; }
+        double step = rho / dAd;
+        double rho_prev = rho;
+        rho = 0.0;
+        for (long k = 0; k < n; ++k) {
+            ys[k] = (fcplx)((cplx)ys[k] + step * (cplx)ds[k]);
+            rs[k] = (fcplx)((cplx)rs[k] - step * (cplx)qs[k]);
+            rho += creal(conj((cplx)rs[k]) * (cplx)rs[k]);
+        }
+        ++it;
+        if (rho > rho_max) rho_max = rho;
+        double mult;
+        if (rho < delta_in * delta_in * rho_max || rho <= goal) {
+            /* reliable update (x += y) and group-wise update (r^ = b - A x) */
+            for (long k = 0; k < n; ++k) x[k] += (cplx)ys[k];
+            apply_A_tmp(L, U, mass, x, ad, wk);
+            for (long k = 0; k < n; ++k) rt[k] = b[k] - ad[k];
+            true2 = re_dot(rt, rt, n);
+            ++ups;
+            if (true2 <= goal) { status = ORC_OK; break; }
+            for (long k = 0; k < n; ++k) { ys[k] = 0.0f; rs[k] = (fcplx)rt[k]; }
+            mult = true2 / rho_prev;        /* Eq. 6 */
+            rho = 0.0;
+            for (long k = 0; k < n; ++k) rho += creal(conj((cplx)rs[k]) * (cplx)rs[k]);
+            rho_max = rho;
+        } else {
+            mult = rho / rho_prev;
+        }
+        for (long k = 0; k < n; ++k) ds[k] = (fcplx)((cplx)rs[k] + mult * (cplx)ds[k]);
+    }
+out:
+    apply_A_tmp(L, U, mass, x, ad, wk);
+    for (long k = 0; k < n; ++k) rt[k] = b[k] - ad[k];
+    res[0] = b2 > 0.0 ? sqrt(re_dot(rt, rt, n) / b2) : 0.0;
+    info[0] = it;
+    info[1] = ups;
+    free(rt); free(ad); free(wk); free(ys); free(rs); free(ds); free(qs);
+    return status;
+}
+
 int orc_version(void) { return 1; }

@@ -1,0 +1,55 @@
+"""The oracle's emulated mixed-precision CG (Fig. 2, Eq. 6, Sec. 3.2:
+single-precision inner vectors, double updates) reaches the same solution as
+its FP64 CG, and behaves as the method says: most iterations in the low
+precision, updates that fire as the residual falls by delta."""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+from lattice_util import free_eigenvalue, momentum, plane_wave, rel
+
+
+def test_c1_same_solution_as_fp64_cg():
+    dims, mass, tol = (4, 4, 4, 4), 0.1, 1e-10
+    U = gen.gauge_field(dims, "haar", seed=0)
+    b = gen.source(dims, seed=1)
+    x64, i64 = oracle.cg(dims, U, mass, b, tol=tol)
+    x, info = oracle.cg_mixed(dims, U, mass, b, tol=tol, delta=0.1)
+    assert info["status"] == 0 and info["true_res"] <= tol
+    kappa = (mass ** 2 + 64) / mass ** 2
+    assert rel(x, x64) <= kappa * tol
+    # single-precision inner iterations cost some extra iterations only
+    assert info["updates"] >= 1 and info["iters"] <= 1.5 * i64["iters"]
+    assert info["low_precision_fraction"] >= 0.95
+
+
+def test_plane_wave_solved_to_closed_form():
+    """U = 1, b a plane wave: A b = lambda b, x = b / lambda (single precision
+    inner steps plus updates reach it to tol)."""
+    dims, mass = (4, 6, 2, 8), 0.3
+    p = momentum(dims, (1, 2, 1, 0))
+    b = plane_wave(dims, p, [0.3 - 0.1j, 1.0, 0.2j])
+    x, info = oracle.cg_mixed(dims, gen.unit_gauge(dims), mass, b, tol=1e-10, delta=0.1)
+    assert info["status"] == 0
+    assert rel(x, b / free_eigenvalue(p, mass)) < 1e-9
+
+
+def test_smaller_delta_fewer_updates():
+    """The trigger |r^| < delta max|r^|: a smaller delta fires less often."""
+    dims, mass = (4, 4, 4, 8), 0.05
+    U = gen.gauge_field(dims, "exp", seed=5, eps=0.5)
+    b = gen.source(dims, seed=6)
+    ups = []
+    for delta in (0.01, 0.1, 0.5):
+        _, info = oracle.cg_mixed(dims, U, mass, b, tol=1e-10, delta=delta)
+        assert info["status"] == 0 and info["true_res"] <= 1e-10
+        ups.append(info["updates"])
+    assert ups[0] <= ups[1] <= ups[2] and ups[0] < ups[2]
+
+
+@pytest.mark.parametrize("delta", [0.0, 1.0, -0.5])
+def test_bad_delta_rejected(delta):
+    dims = (2, 2, 2, 2)
+    with pytest.raises(ValueError):
+        oracle.cg_mixed(dims, gen.unit_gauge(dims), 0.1, gen.source(dims, seed=1), delta=delta)
