@@ -344,3 +344,22 @@ def test_dslash_group_rejects_mixed_reconstruction():
         with pytest.raises(stg.StgError) as e:
             stg.stg_dslash_group([a.handle, b.handle], [0, 0], [f, f], [o1, o2], stg.STG_FP32)
         assert e.value.status == stg.STG_ERR_INVALID_ARG
+
+
+def test_fp32_mixed_cg_follows_the_emulated_method():
+    """C1 with FP32 inner iterations on the GPU against the oracle's
+    emulation of the same method (Fig. 2, Eq. 6, Sec. 3.2; single-precision
+    inner vectors, double updates) at the same delta: both reach tol, their
+    solutions agree within the condition bound, and their iteration counts
+    within a factor 1.5 (rounding orders differ, the method does not)."""
+    dims, mass, tol, delta = (4, 4, 4, 4), 0.1, 1e-10, 0.05
+    U = gen.gauge_field(dims, "haar", seed=0)
+    b = gen.source(dims, seed=1)
+    xe, ie = oracle.cg_mixed(dims, U, mass, b, tol=tol, delta=delta)
+    with Gauge(dims, U, sloppy=stg.STG_FP32, recon=18) as g:
+        x, st = g.cg_solve(_to_dev(b), mass, tol, g.params(delta=delta))
+    x = x.cpu().numpy()
+    _check_solution(dims, U, mass, b, x, tol)
+    kappa = (mass ** 2 + 64) / mass ** 2
+    assert rel(x, xe) <= kappa * tol
+    assert ie["iters"] / 1.5 <= st["iters"] <= 1.5 * ie["iters"], (st["iters"], ie["iters"])
