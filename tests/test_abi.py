@@ -115,3 +115,17 @@ def test_gauge_bytes_counts_every_link_copy(stg, monkeypatch):
     assert stg.stg_gauge_bytes(dims, stg.STG_FX16, 12) == hi + 8 * a256(vh * 24)
     assert stg.stg_gauge_bytes((4, 4, 3, 4), stg.STG_FP32, 12) == 0
     assert stg.stg_gauge_bytes(dims, stg.STG_FP32, 10) == 0
+
+
+def test_group_launch_argument_checks(stg):
+    """stg_dslash_group rejects an empty or oversized group and NULL
+    handles before any CUDA call."""
+    for n in (0, 17):
+        with pytest.raises(stg.StgError) as e:
+            stg.stg_dslash_group([0] * n, [0] * n, [0] * n, [0] * n, stg.STG_FP32, stream=0)
+        assert e.value.status == stg.STG_ERR_INVALID_ARG
+    with pytest.raises(stg.StgError) as e:
+        stg.stg_dslash_group([0], [0], [16], [32], stg.STG_FP32, stream=0)
+    assert e.value.status == stg.STG_ERR_INVALID_ARG
+    with pytest.raises(ValueError):
+        stg.stg_dslash_group([0, 0], [0], [0], [0], stg.STG_FP32, stream=0)
