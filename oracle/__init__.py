@@ -57,7 +57,7 @@ def _load():
         lib.orc_cg.argtypes = [p, p, ctypes.c_double, p, p, ctypes.c_double,
                                ctypes.c_long, ctypes.c_int, p, p]
         lib.orc_cg_mixed.argtypes = [p, p, ctypes.c_double, p, p, ctypes.c_double,
-                                     ctypes.c_double, ctypes.c_long, p, p]
+                                     ctypes.c_double, ctypes.c_long, ctypes.c_int, p, p]
         for f in ("orc_dslash", "orc_dslash_sites", "orc_apply_A", "orc_cg", "orc_cg_mixed"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
@@ -152,9 +152,10 @@ def cg(dims, U, mass: float, b, tol: float = 1e-10, maxiter: int | None = None,
 
 
 def cg_mixed(dims, U, mass: float, b, tol: float = 1e-10, delta: float = 0.1,
-             maxiter: int | None = None, x0=None):
+             maxiter: int | None = None, x0=None, refine: bool = False):
     """Mixed-precision CG (Fig. 2, Eq. 6, Sec. 3.2) emulated with single-
-    precision inner vectors and double updates.
+    precision inner vectors and double updates; refine=True gives Fig. 2's
+    plain iterative refinement (inner solves restart from d = r).
 
     Returns (x, info) with info = dict(status, iters, updates, true_res,
     low_precision_fraction = iters / (iters + updates)).
@@ -168,7 +169,7 @@ def cg_mixed(dims, U, mass: float, b, tol: float = 1e-10, delta: float = 0.1,
     info = np.zeros(2, dtype=np.int64)
     res = np.zeros(1, dtype=np.float64)
     st = lib.orc_cg_mixed(_ptr(dd), _ptr(U), float(mass), _ptr(b), _ptr(x), float(tol),
-                          float(delta), int(maxiter), _ptr(info), _ptr(res))
+                          float(delta), int(maxiter), int(bool(refine)), _ptr(info), _ptr(res))
     _raise(st, "cg_mixed")
     it, up = int(info[0]), int(info[1])
     return x, dict(status=int(st), iters=it, updates=up, true_res=float(res[0]),

@@ -265,6 +265,9 @@ done:
  * trigger: x += y, r = b - A x (double), y = 0, r^ = r (group-wise update);
  * if |r| <= tol |b| the solve ends; else d = r^ + beta d with beta =
  * |r|^2 / (the iterated |r^|^2 before the triggering step) (Eq. 6, d kept).
+ * With refine != 0, the plain iterative refinement of Fig. 2 instead: the
+ * reference is |r^|^2 at the start of the inner solve, and each inner solve
+ * starts again from d = r^.
  *
  * info[0] = inner iterations, info[1] = updates; res[0] = |b - A x| / |b|.
  * Returns ORC_OK, ORC_NOT_CONVERGED or ORC_BREAKDOWN (d^dag A d <= 0).
@@ -272,7 +275,7 @@ done:
 typedef float complex fcplx;
 
 int orc_cg_mixed(const int *L, const cplx *U, double mass, const cplx *b, cplx *x,
-                 double tol, double delta_in, long maxiter, long *info, double *res)
+                 double tol, double delta_in, long maxiter, int refine, long *info, double *res)
 {
     int e = check_dims(L);
     if (e) return e;
@@ -328,7 +331,7 @@ int orc_cg_mixed(const int *L, const cplx *U, double mass, const cplx *b, cplx *
             rho += creal(conj((cplx)rs[k]) * (cplx)rs[k]);
         }
         ++it;
-        if (rho > rho_max) rho_max = rho;
+        if (!refine && rho > rho_max) rho_max = rho;
         double mult;
         if (rho < delta_in * delta_in * rho_max || rho <= goal) {
             /* reliable update (x += y) and group-wise update (r^ = b - A x) */
@@ -339,7 +342,7 @@ int orc_cg_mixed(const int *L, const cplx *U, double mass, const cplx *b, cplx *
             ++ups;
             if (true2 <= goal) { status = ORC_OK; break; }
             for (long k = 0; k < n; ++k) { ys[k] = 0.0f; rs[k] = (fcplx)rt[k]; }
-            mult = true2 / rho_prev;        /* Eq. 6 */
+            mult = refine ? 0.0 : true2 / rho_prev;   /* Eq. 6; Fig. 2 restarts d */
             rho = 0.0;
             for (long k = 0; k < n; ++k) rho += creal(conj((cplx)rs[k]) * (cplx)rs[k]);
             rho_max = rho;

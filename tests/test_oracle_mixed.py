@@ -53,3 +53,17 @@ def test_bad_delta_rejected(delta):
     dims = (2, 2, 2, 2)
     with pytest.raises(ValueError):
         oracle.cg_mixed(dims, gen.unit_gauge(dims), 0.1, gen.source(dims, seed=1), delta=delta)
+
+
+def test_refinement_variant_converges_and_restarts_cost_iterations():
+    """Fig. 2's plain refinement (d restarted at each update) reaches the same
+    solution; keeping d through the update (Eq. 6) needs no more iterations."""
+    dims, mass, tol = (4, 4, 4, 8), 0.05, 1e-10
+    U = gen.gauge_field(dims, "exp", seed=5, eps=0.5)
+    b = gen.source(dims, seed=6)
+    xr, ir = oracle.cg_mixed(dims, U, mass, b, tol=tol, delta=0.1, refine=True)
+    xe, ie = oracle.cg_mixed(dims, U, mass, b, tol=tol, delta=0.1)
+    assert ir["status"] == 0 and ir["true_res"] <= tol and ir["updates"] >= 1
+    kappa = (mass ** 2 + 64) / mass ** 2
+    assert rel(xr, xe) <= 2 * kappa * tol
+    assert ie["iters"] <= ir["iters"]
