@@ -13,9 +13,16 @@ Prints one JSON line (rank 0).  `value` = solves per second over all ranks
 time of the GPU's own plain FP64 CG on the same system, the roofline of the
 dominant kernel from CUDA events recorded inside the solver's graph, an
 end-to-end figure with host buffers, the clocks seen during the timed region
-and the FP64 CPU oracle timed on the host cores.
+and the FP64 CPU oracle timed on the host cores (a projection from a bounded
+sample, checked against complete 16^3 x 32 solves).  After the timed region
+the line also carries bounded measurements of the metric's other parts:
+`c3_fp16` (the same solve with IEEE FP16 storage), `c4` (16 systems on
+24^3 x 48 batched against one by one, and the multi-system Dslash's GB/s)
+and `c5` (a served Poisson stream: saturation, then p50 / p99 at 0.7 of it).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl stg|reference]
+  python bench.py --no-extras                 # c3 only
+  python bench.py --workload c4|c5            # the full c4 / c5 runs, own line
   python bench.py --kernels-only --reps 3     # kernels alone (for ncu)
 """
 from __future__ import annotations
@@ -81,7 +88,24 @@ def parse():
                     help="c5: further offered loads (fractions of saturation) to report")
     ap.add_argument("--nrhs", type=int, default=16)
     ap.add_argument("--reps", type=int, default=3)
-    return ap.parse_args()
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the bounded batched (c4), serving (c5) and FP16-storage "
+                         "measurements that the default line carries beside c3")
+    ap.add_argument("--c4-sloppy", default=None, choices=["f32", "fx16", "f16"],
+                    help="c4 inner storage (default: the faster of the library's batched "
+                         "paths, f32)")
+    ap.add_argument("--c5-sloppy", default=None, choices=["f32", "fx16"],
+                    help="c5 inner storage (default: f32)")
+    ap.add_argument("--c5-requests", type=int, default=300,
+                    help="requests per Poisson stream of the bounded c5 measurement")
+    ap.add_argument("--c5-sat-requests", type=int, default=200,
+                    help="requests of the bounded c5 saturation run")
+    args = ap.parse_args()
+    if args.c4_sloppy is None:
+        args.c4_sloppy = "f32"
+    if args.c5_sloppy is None:
+        args.c5_sloppy = "f32"
+    return args
 
 
 def dist_env():
@@ -199,9 +223,10 @@ def dslash_bytes(vh, prec, recon, extra_fields):
 # ---------------------------------------------------------------------------
 # CPU oracle (baseline and reference arm)
 # ---------------------------------------------------------------------------
-def oracle_sample(dims, U, mass, b, fp64_iters, budget_s, one_thread_s=0.0):
-    """Time the FP64 oracle CG (as it stands) for a bounded number of
-    iterations on the full lattice and scale to a complete solve."""
+def _oracle_per_iter(dims, U, mass, b, budget_s):
+    """Seconds per FP64 CG iteration of the oracle (as it stands) on the full
+    lattice, from a bounded run; also the time of a 1-iteration call (setup
+    and the two true-residual applications of A included)."""
     import oracle
     oracle.build()
     oracle.cg(dims, U, mass, b, tol=0.0, maxiter=1, max_restarts=0)   # warm-up
@@ -215,32 +240,87 @@ def oracle_sample(dims, U, mass, b, fp64_iters, budget_s, one_thread_s=0.0):
     per_iter = (tn - t1) / (n - 1)
     if per_iter <= 0.0:                     # timer noise on tiny lattices
         per_iter = tn / n
-    solve_s = max(per_iter * fp64_iters + max(t1 - per_iter, 0.0), tn)
+    return per_iter, t1, n, tn
+
+
+def _projected(per_iter, t1, tn, iters):
+    return max(per_iter * iters + max(t1 - per_iter, 0.0), tn)
+
+
+class _OmpThreads:
+    """Sets the OpenMP thread count of the oracle library for a scope."""
+
+    def __init__(self, n):
+        import ctypes
+        self.n = n
+        try:
+            self.gomp = ctypes.CDLL("libgomp.so.1")
+        except OSError:
+            self.gomp = None
+        self.cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+
+    def __enter__(self):
+        if self.gomp is not None:
+            self.gomp.omp_set_num_threads(self.n)
+        return self
+
+    def __exit__(self, *exc):
+        if self.gomp is not None:
+            self.gomp.omp_set_num_threads(self.cores)
+
+
+def oracle_sample(dims, U, mass, b, fp64_iters, budget_s, one_thread_s=0.0):
+    """Time the FP64 oracle CG (as it stands) for a bounded number of
+    iterations on the full lattice and scale to a complete solve."""
+    import oracle
+    per_iter, t1, n, tn = _oracle_per_iter(dims, U, mass, b, budget_s)
+    solve_s = _projected(per_iter, t1, tn, fp64_iters)
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     out = {"value": 1.0 / solve_s, "unit": "solves/s", "cores": cores, "kind": "oracle",
            "sample": f"{n} FP64 CG iterations of the oracle on the full {dims} lattice "
-                     f"({tn:.1f} s), scaled to {fp64_iters} iterations (the GPU FP64 CG count)",
-           "seconds_per_solve": solve_s}
+                     f"({tn:.1f} s), scaled to {fp64_iters} iterations (the GPU FP64 CG count); "
+                     f"a projection, checked against complete solves in projection_check",
+           "seconds_per_solve": solve_s, "projected": True}
     if one_thread_s > 0:
         # the same oracle on one core (OpenMP runtime of the oracle library)
-        import ctypes
-        try:
-            gomp = ctypes.CDLL("libgomp.so.1")
-        except OSError:
-            gomp = None
-        if gomp is not None:
-            gomp.omp_set_num_threads(1)
-            try:
+        with _OmpThreads(1) as omp:
+            if omp.gomp is not None:
                 m = max(2, min(50, int(one_thread_s / max(per_iter * cores, 1e-6))))
                 t0 = time.perf_counter()
                 oracle.cg(dims, U, mass, b, tol=0.0, maxiter=m, max_restarts=0)
                 t1m = time.perf_counter() - t0
-            finally:
-                gomp.omp_set_num_threads(cores)
-            solve1 = t1m / m * fp64_iters
-            out["value_1_thread"] = 1.0 / solve1
-            out["sample_1_thread"] = (f"{m} FP64 CG iterations on one core ({t1m:.1f} s), scaled "
-                                      f"to {fp64_iters} iterations")
+                solve1 = t1m / m * fp64_iters
+                out["value_1_thread"] = 1.0 / solve1
+                out["sample_1_thread"] = (f"{m} FP64 CG iterations on one core ({t1m:.1f} s), "
+                                          f"scaled to {fp64_iters} iterations")
+    return out
+
+
+C2 = {"dims": (16, 16, 16, 32), "mass": 0.01, "eps": 0.4, "tol": 1e-10}
+
+
+def projection_check(one_thread: bool):
+    """The per-iteration projection against complete solves: the oracle's
+    FP64 CG of 16^3 x 32 (m = 0.01, exp(i 0.4 H) links, tol 1e-10) run to
+    convergence on all host cores (and on one core), beside the time that the
+    same bounded-sample projection gives for it."""
+    import gen
+    import oracle
+    dims, mass = C2["dims"], C2["mass"]
+    U = gen.gauge_field(dims, "exp", seed=0, eps=C2["eps"])
+    b = gen.source(dims, seed=1)
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    out = {"lattice": "16x16x16x32", "mass": mass, "tol": C2["tol"]}
+    runs = [("all_cores", cores)] + ([("one_core", 1)] if one_thread else [])
+    for name, nt in runs:
+        with _OmpThreads(nt):
+            per_iter, t1, n, tn = _oracle_per_iter(dims, U, mass, b, 1.0 if nt > 1 else 3.0)
+            t0 = time.perf_counter()
+            _, info = oracle.cg(dims, U, mass, b, tol=C2["tol"])
+            full = time.perf_counter() - t0
+        proj = _projected(per_iter, t1, tn, info["iters"])
+        out[name] = {"threads": nt, "iters": info["iters"], "full_solve_s": full,
+                     "projected_s": proj, "sample_iters": n, "full_over_projected": full / proj}
     return out
 
 
@@ -252,27 +332,39 @@ def gen_inputs(dims, eps, rank):
 
 
 def run_reference(args, dims):
+    """The reference arm: the FP64 oracle CG timed on the host cores.  Each
+    step is a bounded sample (a fixed number of iterations on the full
+    lattice) whose per-iteration time projects a complete solve; ms_per_step
+    is the measured duration of one such step, and `value` the projected
+    solves/s.  The projection is checked once against complete solves of
+    16^3 x 32 on all cores and on one core."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
     U, b = gen_inputs(dims, args.eps, 0)
     fp64_iters = 2552 if dims == (32, 32, 32, 64) else 3 * (dims[0] * dims[1] * dims[2] * dims[3] // 2)
-    per_step = max(5.0, 60.0 / max(1, args.steps + args.warmup))
+    per_step = max(4.0, 40.0 / max(1, args.steps + args.warmup))
     for _ in range(args.warmup):
-        oracle_sample(dims, U, args.mass, b, fp64_iters, min(per_step, 5.0))
-    vals = []
+        oracle_sample(dims, U, args.mass, b, fp64_iters, min(per_step, 4.0))
+    vals, walls = [], []
     for _ in range(args.steps):
+        t0 = time.perf_counter()
         vals.append(oracle_sample(dims, U, args.mass, b, fp64_iters, per_step))
+        walls.append(time.perf_counter() - t0)
     v = statistics.median(x["value"] for x in vals)
     cb = dict(vals[-1])
     cb["value"] = v
-    ms = 1000.0 / v
+    check = projection_check(one_thread=True)
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s",
-        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * statistics.mean(walls),
+        "ms_per_step_meaning": "wall time of one bounded sample step (not of a solve)",
+        "ms_per_solve_projected": 1000.0 / v,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": config_dict(args, dims),
         "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
+        "projection_check": check,
         "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
@@ -293,7 +385,9 @@ def config_dict(args, dims):
 # ---------------------------------------------------------------------------
 # c4: one gauge field, 16 systems with masses log-uniform in [0.005, 0.05]
 # ---------------------------------------------------------------------------
-def run_c4(args):
+def c4_measure(args, steps, warmup, one_by_one_reps=1):
+    """Batched solve of 16 systems on 24^3 x 48 against the same systems
+    solved one by one, and the multi-system Dslash alone (GB/s)."""
     import numpy as np
     import torch
 
@@ -307,12 +401,13 @@ def run_c4(args):
     masses = gen.log_uniform(n, 0.005, 0.05, seed=17)
     bs = gen.source(dims, seed=1, nrhs=n)
     vh = bs.shape[1]
-    sloppy = {"f32": stg.STG_FP32, "fx16": stg.STG_FX16, "f16": stg.STG_FP16}[args.sloppy]
+    c4_sloppy = args.c4_sloppy or args.sloppy
+    sloppy = {"f32": stg.STG_FP32, "fx16": stg.STG_FX16, "f16": stg.STG_FP16}[c4_sloppy]
     g = stg.Gauge(dims, U, sloppy=sloppy, recon=args.recon)
     stream = torch.cuda.current_stream()
     src = torch.from_numpy(np.ascontiguousarray(bs)).to(dev)
     p = g.params(policy=stg.STG_CG_RELIABLE, sloppy=sloppy)
-    if args.delta is not None:
+    if args.delta is not None and args.workload == "c4":
         p.delta = args.delta
 
     def batched():
@@ -326,24 +421,27 @@ def run_c4(args):
             out.append(stg.stg_cg_solve(g.handle, src[k], x, masses[k], args.tol, p, stream))
         return out
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         batched()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     clocks = ClockSampler("")
     e0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         st = batched()
     e1.record(stream)
     torch.cuda.synchronize()
     ck = clocks.stop()
-    t_batch = e0.elapsed_time(e1) / 1000.0 / args.steps
+    t_batch = e0.elapsed_time(e1) / 1000.0 / steps
     one_by_one()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    single = one_by_one()
-    torch.cuda.synchronize()
-    t_single = time.perf_counter() - t0
+    singles = []
+    for _ in range(one_by_one_reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        single = one_by_one()
+        torch.cuda.synchronize()
+        singles.append(time.perf_counter() - t0)
+    t_single = statistics.median(singles)
     # the multi-system Dslash alone, back to back on this stream
     fb = stg.stg_field_bytes(g.handle, sloppy)
     fin = torch.empty(n * fb, dtype=torch.uint8, device=dev)
@@ -359,23 +457,20 @@ def run_c4(args):
     s1.record(stream)
     s1.synchronize()
     t_m = s0.elapsed_time(s1) / 20
-    L, S = LINK_BYTES[(args.sloppy, args.recon)], FIELD_BYTES[args.sloppy]
+    L, S = LINK_BYTES[(c4_sloppy, args.recon)], FIELD_BYTES[c4_sloppy]
     # links once per NB x TPS systems (register-fed), once for all (staged, tb = 0)
     link_passes = 1 if tb == 0 else -(-n // (nb * tb))
     nbytes = vh * (8 * L * link_passes + 2 * S * n)
     peak, src_ = measured_hbm()
     achieved = nbytes / (t_m / 1000.0) / 1e9
-    print(json.dumps({
-        "metric": METRIC, "workload": "c4: 24^3x48, 16 systems batched, masses log-uniform "
-                                      "[0.005, 0.05], tol 1e-10",
-        "value": n / t_batch, "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1000.0 * t_batch, "higher_is_better": True,
-        "dtype": "f32", "data": "synthetic",
-        "config": {"lattice": "24x24x24x48", "nrhs": n, "sloppy_storage": args.sloppy,
-                   "recon": args.recon, "masses": [round(float(m), 6) for m in masses],
-                   "links": "exp(i*0.5*H), seed 0", "sources": "seed 1, drawn in sequence"},
-        "batched_seconds": t_batch, "one_by_one_seconds": t_single,
+    g.close()
+    return {
+        "workload": "24^3x48, 16 systems batched, masses log-uniform [0.005, 0.05], tol 1e-10",
+        "solves_per_s": n / t_batch, "batched_ms": 1000.0 * t_batch, "steps": steps,
+        "warmup": warmup, "one_by_one_ms": 1000.0 * t_single,
         "speedup_batched_vs_one_by_one": t_single / t_batch,
+        "sloppy_storage": c4_sloppy, "recon": args.recon,
+        "masses": [round(float(m), 6) for m in masses],
         "iters": [s_["iters"] for s_ in st], "updates": [s_["updates"] for s_ in st],
         "true_res_max": max(s_["true_res"] for s_ in st),
         "iters_one_by_one": [s_["iters"] for s_ in single],
@@ -388,6 +483,21 @@ def run_c4(args):
                         "frac": achieved / peak,
                         "gflops_576": vh * n * 576 / (t_m / 1000.0) / 1e9},
         "clocks": ck,
+    }
+
+
+def run_c4(args):
+    r = c4_measure(args, args.steps, args.warmup, one_by_one_reps=1)
+    print(json.dumps({
+        "metric": METRIC, "workload": "c4: " + r["workload"],
+        "value": r["solves_per_s"], "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r["batched_ms"], "higher_is_better": True,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"lattice": "24x24x24x48", "nrhs": args.nrhs,
+                   "sloppy_storage": r["sloppy_storage"], "recon": args.recon,
+                   "masses": r["masses"], "links": "exp(i*0.5*H), seed 0",
+                   "sources": "seed 1, drawn in sequence"},
+        **{k: v for k, v in r.items() if k not in ("workload", "masses")},
     }), flush=True)
 
 
@@ -416,7 +526,9 @@ def c5_requests(n, rate, seed=2000):
                     float(mass[i]), float(tol[i])) for i in range(n)]
 
 
-def run_c5(args):
+def c5_measure(args, n_requests, sat_requests, loads, warm_requests=64):
+    """Saturation throughput (every request at t = 0), then Poisson streams
+    at fractions `loads` of it; the headline load is args.load."""
     import numpy as np
     import torch
 
@@ -430,60 +542,106 @@ def run_c5(args):
             gauges[(li, j)] = (dims, gen.gauge_field(dims, "exp", seed=10 * li + j, eps=0.5))
         for j in range(4):
             sources[(li, j)] = gen.source(dims, seed=1000 + 10 * li + j)
-    sloppy = {"f32": stg.STG_FP32, "fx16": stg.STG_FX16}[args.sloppy]
+    c5_sloppy = args.c5_sloppy or args.sloppy
+    sloppy = {"f32": stg.STG_FP32, "fx16": stg.STG_FX16}[c5_sloppy]
     eng = ServeEngine(gauges, sources, hbm_budget=120e9, slots=args.slots,
                       max_sessions_per_gauge=args.sessions,
                       max_resident=8, sloppy=sloppy, recon=args.recon,
                       priority_by_size=not args.no_priority, chunk=args.chunk)
     try:
-        eng.run(c5_requests(64, None, seed=7), realtime=False)       # warm-up, tuning
-        sat_res = eng.run(c5_requests(args.requests, None), realtime=False)
+        eng.run(c5_requests(warm_requests, None, seed=7), realtime=False)   # warm-up, tuning
+        sat_res = eng.run(c5_requests(sat_requests, None), realtime=False)
         sat = summarize(sat_res)
-        # the offered rate swept below the saturation throughput; the
-        # headline is args.load (0.7)
         sweep = []
-        for load in sorted({*args.sweep, args.load}):
+        for load in sorted({*loads, args.load}):
             r_ = load * sat["solves_per_s"]
             if args.rate > 0:   # an absolute offered rate (requests / s) instead
                 r_ = args.rate * load / args.load
             clocks = ClockSampler("")
-            res_ = eng.run(c5_requests(args.requests, r_), realtime=True)
+            res_ = eng.run(c5_requests(n_requests, r_), realtime=True)
             ck_ = clocks.stop()
             sm_ = summarize(res_)
             sweep.append({"load": load, "offered_rate": r_, "solves_per_s": sm_["solves_per_s"],
                           "p50_ms": sm_["p50_ms"], "p99_ms": sm_["p99_ms"], "ok": sm_["ok"]})
             if load == args.load:
                 res, rate, ck = res_, r_, ck_
+        peak_used, peak_measured = eng.peak_used, eng.peak_measured
     finally:
         eng.close()
     summ = summarize(res)
     per = {}
-    reqs = c5_requests(args.requests, rate)     # the same stream, for per-lattice stats
+    reqs = c5_requests(n_requests, rate)     # the same stream, for per-lattice stats
     for li, (dims, _) in enumerate(C5_LATTICES):
         ls = np.array([r.latency for r, q in zip(res, reqs) if q.gauge_key[0] == li])
         if ls.size:
             per["x".join(map(str, dims))] = {"n": int(ls.size),
                                                "p50_ms": 1e3 * float(np.percentile(ls, 50)),
                                                "p99_ms": 1e3 * float(np.percentile(ls, 99))}
-    print(json.dumps({
-        "metric": METRIC, "workload": "c5: Poisson stream of solve requests, continuous batching",
-        "value": summ["solves_per_s"], "unit": "solves/s", "n_gpus": 1,
-        "higher_is_better": True, "dtype": "f32", "data": "synthetic",
-        "config": {"requests": args.requests, "lattices": {"x".join(map(str, d)): w
-                                                           for d, w in C5_LATTICES},
+    return {
+        "workload": "Poisson stream of solve requests, continuous batching",
+        "requests": n_requests, "saturation_requests": sat_requests,
+        "solves_per_s": summ["solves_per_s"], "p50_ms": summ["p50_ms"], "p99_ms": summ["p99_ms"],
+        "mean_ms": summ["mean_ms"], "ok": summ["ok"], "offered_rate": rate,
+        "load_vs_saturation": args.load, "saturation": sat, "load_sweep": sweep,
+        "per_lattice": per,
+        "max_true_res_over_tol": max(r.true_res / q.tol for r, q in zip(res, reqs)),
+        "hbm_budget_gb": 120, "peak_counted_gb": peak_used / 1e9,
+        "peak_measured_gb": peak_measured / 1e9,
+        "config": {"lattices": {"x".join(map(str, d)): w for d, w in C5_LATTICES},
                    "gauge_fields": 8, "sources_per_lattice": 4,
                    "mass": "log-uniform [0.005, 0.1]", "tol": "1e-8 or 1e-10",
-                   "hbm_budget_gb": 120, "slots_per_session": args.slots,
-                   "sessions_per_gauge": args.sessions,
+                   "slots_per_session": args.slots, "sessions_per_gauge": args.sessions,
                    "stream_priority_by_lattice_size": not args.no_priority,
-                   "iterations_per_step": args.chunk,
-                   "sloppy_storage": args.sloppy, "offered_rate": rate,
-                   "load_vs_saturation": args.load},
-        "p50_ms": summ["p50_ms"], "p99_ms": summ["p99_ms"], "mean_ms": summ["mean_ms"],
-        "ok": summ["ok"], "saturation": sat, "load_sweep": sweep, "per_lattice": per,
-        "max_true_res_over_tol": max(r.true_res / q.tol for r, q in zip(res, reqs)),
+                   "iterations_per_step": args.chunk, "sloppy_storage": c5_sloppy},
         "clocks": ck,
+    }
+
+
+def run_c5(args):
+    r = c5_measure(args, args.requests, args.requests, args.sweep)
+    cfg = dict(r.pop("config"))
+    cfg.update({"requests": args.requests, "hbm_budget_gb": 120, "offered_rate": r["offered_rate"],
+                "load_vs_saturation": args.load})
+    print(json.dumps({
+        "metric": METRIC, "workload": "c5: " + r["workload"],
+        "value": r["solves_per_s"], "unit": "solves/s", "n_gpus": 1,
+        "higher_is_better": True, "dtype": "f32", "data": "synthetic", "config": cfg,
+        **{k: v for k, v in r.items() if k != "workload"},
     }), flush=True)
+
+
+def c3_fp16_measure(args, dims, U, b_np):
+    """C3 as the configuration states it: IEEE FP16 storage of links and
+    fields (per-site scale), 12-real links, FP32 compute, FP64 reliable
+    updates; one complete solve timed with CUDA events (its graphs captured
+    by an untimed short solve first)."""
+    import torch
+    import paper_1111_0125_gb300 as stg
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    b = torch.from_numpy(b_np).to(dev)
+    with stg.Gauge(dims, U, sloppy=stg.STG_FP16, recon=12) as g:
+        p = g.params(policy=stg.STG_CG_RELIABLE, sloppy=stg.STG_FP16)
+        warm = g.params(policy=stg.STG_CG_RELIABLE, sloppy=stg.STG_FP16, maxiter=64)
+        try:
+            stg.stg_cg_solve(g.handle, b, torch.zeros_like(b), args.mass, args.tol, warm, stream)
+        except stg.StgError:
+            pass
+        x = torch.zeros_like(b)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        status, st = "ok", None
+        try:
+            st = stg.stg_cg_solve(g.handle, b, x, args.mass, args.tol, p, stream)
+        except stg.StgError as err:
+            status, st = stg.stg_status_string(err.status), err.stats
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return {"storage": "f16 (IEEE binary16, per-site scale), 12-real links",
+                "status": status, "seconds": e0.elapsed_time(e1) / 1000.0,
+                "iters": st["iters"], "updates": st["updates"], "true_res": st["true_res"],
+                "delta": p.delta}
 
 
 # ---------------------------------------------------------------------------
@@ -653,11 +811,20 @@ def main():
     achieved = nbytes / (tk / 1000.0) / 1e9
     iters = statistics.mean(s["iters"] for s in stats)
     updates = statistics.mean(s["updates"] for s in stats)
+    extras = {}
+    if not args.no_extras and world == 1:
+        # bounded measurements of the metric's other parts, after the timed
+        # region: FP16 storage as C3 states it, the batched C4 and the
+        # served C5 stream
+        extras["c3_fp16"] = c3_fp16_measure(args, dims, U, b_np)
+        extras["c4"] = c4_measure(args, steps=2, warmup=1)
+        extras["c5"] = c5_measure(args, args.c5_requests, args.c5_sat_requests, loads=[])
     cpu = None
     if not args.no_cpu and world == 1:
         cpu = oracle_sample(dims, U, args.mass, b_np, fp64["iters"] if fp64 else 2552,
                             args.cpu_seconds, one_thread_s=6.0)
         cpu.pop("seconds_per_solve")
+        cpu["projection_check"] = projection_check(one_thread=True)
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
@@ -689,6 +856,7 @@ def main():
         "gpu_launches": int(sum(s["launches"] for s in stats)),
         "clocks": ck,
     }
+    line.update(extras)
     print(json.dumps(line), flush=True)
 
 

@@ -213,8 +213,10 @@ stg_status stg_dslash(const stg_gauge *g, int out_parity, const void *in_dev,
  * output is bitwise the one of stg_dslash where that runs the one-site-per-
  * thread kernel (every precision but FX16 / 12-real, whose stg_dslash runs
  * the packed staged kernel: agreement to rounding); the group runs as one
- * grid, which fills the GPU where one small lattice would not.  Arrays are host arrays of n entries; fields as for stg_dslash (no
- * item's output may alias any item's input).  The paper applies the
+ * grid, which fills the GPU where one small lattice would not.  Arrays
+ * are host arrays of n entries; fields as for stg_dslash.  No item's output
+ * may alias any item's input: an output pointer equal to any in_dev[j]
+ * returns STG_ERR_INVALID_ARG (partial overlaps are not detected).  The paper applies the
  * operator to one lattice at a time; this is a serving-layer form of it.
  * Errors: STG_ERR_INVALID_ARG, STG_ERR_UNSUPPORTED, STG_ERR_CUDA.
  */

@@ -58,6 +58,9 @@ def _load():
                                ctypes.c_long, ctypes.c_int, p, p]
         lib.orc_cg_mixed.argtypes = [p, p, ctypes.c_double, p, p, ctypes.c_double,
                                      ctypes.c_double, ctypes.c_long, ctypes.c_int, p, p]
+        lib.orc_cg_mixed_snap.argtypes = [p, p, ctypes.c_double, p, p, ctypes.c_double,
+                                          ctypes.c_double, ctypes.c_long, ctypes.c_int, p, p,
+                                          p, p]
         for f in ("orc_dslash", "orc_dslash_sites", "orc_apply_A", "orc_cg", "orc_cg_mixed"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
@@ -152,13 +155,19 @@ def cg(dims, U, mass: float, b, tol: float = 1e-10, maxiter: int | None = None,
 
 
 def cg_mixed(dims, U, mass: float, b, tol: float = 1e-10, delta: float = 0.1,
-             maxiter: int | None = None, x0=None, refine: bool = False):
+             maxiter: int | None = None, x0=None, refine: bool = False,
+             snapshot: bool = False):
     """Mixed-precision CG (Fig. 2, Eq. 6, Sec. 3.2) emulated with single-
     precision inner vectors and double updates; refine=True gives Fig. 2's
     plain iterative refinement (inner solves restart from d = r).
 
     Returns (x, info) with info = dict(status, iters, updates, true_res,
-    low_precision_fraction = iters / (iters + updates)).
+    low_precision_fraction = iters / (iters + updates)).  With snapshot=True,
+    info["first_update"] holds the state around the first reliable update
+    that does not end the solve (None if there is none): rho_prev and
+    rho_iter (the iterated |r^|^2 before and after the triggering step),
+    true2 (|r|^2 of the new true residual), and the vectors x (after the
+    update), d_old, r_hat (after it) and d_new.
     """
     lib = _load()
     dd, U, b = _dims(dims), _c128(U), _c128(b)
@@ -168,9 +177,19 @@ def cg_mixed(dims, U, mass: float, b, tol: float = 1e-10, delta: float = 0.1,
         maxiter = 10 * 3 * _vh(dims)
     info = np.zeros(2, dtype=np.int64)
     res = np.zeros(1, dtype=np.float64)
-    st = lib.orc_cg_mixed(_ptr(dd), _ptr(U), float(mass), _ptr(b), _ptr(x), float(tol),
-                          float(delta), int(maxiter), int(bool(refine)), _ptr(info), _ptr(res))
+    snap_s = np.zeros(4, dtype=np.float64)
+    snap_v = np.zeros((4,) + b.shape, dtype=np.complex128) if snapshot else None
+    st = lib.orc_cg_mixed_snap(_ptr(dd), _ptr(U), float(mass), _ptr(b), _ptr(x), float(tol),
+                               float(delta), int(maxiter), int(bool(refine)), _ptr(info),
+                               _ptr(res), _ptr(snap_s) if snapshot else None,
+                               _ptr(snap_v) if snapshot else None)
     _raise(st, "cg_mixed")
     it, up = int(info[0]), int(info[1])
-    return x, dict(status=int(st), iters=it, updates=up, true_res=float(res[0]),
-                   low_precision_fraction=it / max(1, it + up))
+    out = dict(status=int(st), iters=it, updates=up, true_res=float(res[0]),
+               low_precision_fraction=it / max(1, it + up))
+    if snapshot:
+        out["first_update"] = None if snap_s[3] == 0.0 else dict(
+            rho_prev=float(snap_s[0]), rho_iter=float(snap_s[1]), true2=float(snap_s[2]),
+            x=snap_v[0].copy(), d_old=snap_v[1].copy(), r_hat=snap_v[2].copy(),
+            d_new=snap_v[3].copy())
+    return x, out

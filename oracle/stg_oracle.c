@@ -271,11 +271,19 @@ done:
  *
  * info[0] = inner iterations, info[1] = updates; res[0] = |b - A x| / |b|.
  * Returns ORC_OK, ORC_NOT_CONVERGED or ORC_BREAKDOWN (d^dag A d <= 0).
+ *
+ * Optional snapshot of the first update that does not end the solve (for
+ * the test of Eq. 6; both NULL otherwise): snap_s[0] = the iterated |r^|^2
+ * before the triggering step, snap_s[1] = the iterated |r^|^2 after it,
+ * snap_s[2] = |r|^2 of the new true residual, snap_s[3] = 1 once taken;
+ * snap_v = 4 n values: x after the update, d before it, r^ after it and the
+ * new d.  Recording changes none of the arithmetic.
  */
 typedef float complex fcplx;
 
-int orc_cg_mixed(const int *L, const cplx *U, double mass, const cplx *b, cplx *x,
-                 double tol, double delta_in, long maxiter, int refine, long *info, double *res)
+int orc_cg_mixed_snap(const int *L, const cplx *U, double mass, const cplx *b, cplx *x,
+                      double tol, double delta_in, long maxiter, int refine, long *info,
+                      double *res, double *snap_s, cplx *snap_v)
 {
     int e = check_dims(L);
     if (e) return e;
@@ -342,14 +350,29 @@ int orc_cg_mixed(const int *L, const cplx *U, double mass, const cplx *b, cplx *
             ++ups;
             if (true2 <= goal) { status = ORC_OK; break; }
             for (long k = 0; k < n; ++k) { ys[k] = 0.0f; rs[k] = (fcplx)rt[k]; }
+            const int snap = snap_s && snap_v && snap_s[3] == 0.0;
+            if (snap) {
+                snap_s[0] = rho_prev;
+                snap_s[1] = rho;
+                snap_s[2] = true2;
+                snap_s[3] = 1.0;
+                for (long k = 0; k < n; ++k) {
+                    snap_v[k] = x[k];
+                    snap_v[n + k] = (cplx)ds[k];
+                    snap_v[2 * n + k] = (cplx)rs[k];
+                }
+            }
             mult = refine ? 0.0 : true2 / rho_prev;   /* Eq. 6; Fig. 2 restarts d */
+            for (long k = 0; k < n; ++k) ds[k] = (fcplx)((cplx)rs[k] + mult * (cplx)ds[k]);
+            if (snap)
+                for (long k = 0; k < n; ++k) snap_v[3 * n + k] = (cplx)ds[k];
             rho = 0.0;
             for (long k = 0; k < n; ++k) rho += creal(conj((cplx)rs[k]) * (cplx)rs[k]);
             rho_max = rho;
         } else {
             mult = rho / rho_prev;
+            for (long k = 0; k < n; ++k) ds[k] = (fcplx)((cplx)rs[k] + mult * (cplx)ds[k]);
         }
-        for (long k = 0; k < n; ++k) ds[k] = (fcplx)((cplx)rs[k] + mult * (cplx)ds[k]);
     }
 out:
     apply_A_tmp(L, U, mass, x, ad, wk);
@@ -359,6 +382,13 @@ out:
     info[1] = ups;
     free(rt); free(ad); free(wk); free(ys); free(rs); free(ds); free(qs);
     return status;
+}
+
+int orc_cg_mixed(const int *L, const cplx *U, double mass, const cplx *b, cplx *x,
+                 double tol, double delta_in, long maxiter, int refine, long *info, double *res)
+{
+    return orc_cg_mixed_snap(L, U, mass, b, x, tol, delta_in, maxiter, refine, info, res,
+                             NULL, NULL);
 }
 
 int orc_version(void) { return 1; }

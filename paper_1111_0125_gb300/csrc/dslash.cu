@@ -114,7 +114,8 @@ stg_status launch_dslash(const Geom &g, int prec, int epi, const DslashLaunch &L
         a.lb[mu] = L.links->blk(1 - L.out_parity, mu);
     }
     a.lt = L.links->tiled ? L.links->tiled + (size_t)L.out_parity * L.links->tiled_parity_bytes : nullptr;
-    a.drop_fill = 0;
+    a.grid_cap = L.links->fx_grid_cap;
+    a.drop_fill = L.links->fx_drop_fill;
     a.in = L.in;
     a.out = L.out;
     a.w = L.w;

@@ -16,8 +16,6 @@
 // (32767 U); the sum is scaled by 1/32767 at the end, and the 12-real row 2
 // c = r0 x r1 enters the products with the factor s / 32767 (s the folded
 // phase), i.e. U_2b = (s / 32767) conj(c_b).
-#include <stdlib.h>
-
 #include "stg_internal.h"
 
 #ifndef STG_FX2_MINBLOCKS
@@ -555,20 +553,15 @@ static void launch_staged(const DslashArgs &a, cudaStream_t s, bool pdl)
         if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
         return n;
     }();
-    // STG_FX16_GRID caps the CTA count (more tiles per CTA; for tests)
+    // a.grid_cap (STG_FX16_GRID at handle creation) caps the CTA count, so
+    // that each CTA walks more tiles (tests); a.drop_fill is the failure-
+    // detection test's withheld fill (a CTA's wait for its second tile runs
+    // out after about a second; no fault, no hang)
     int cap = sms * kFxCtasPerSM;
-    if (const char *v = getenv("STG_FX16_GRID")) {
-        const int n = atoi(v);
-        if (n > 0 && n < cap) cap = n;
-    }
+    if (a.grid_cap > 0 && a.grid_cap < cap) cap = a.grid_cap;
     const int ntiles = (a.g.Vh + kFxTile - 1) / kFxTile;
     const int grid = ntiles < cap ? ntiles : cap;
-    // STG_FX16_TEST_DROP_FILL=1: the failure-detection test (a CTA's wait
-    // for its second tile runs out after about a second; no fault, no hang)
-    DslashArgs b = a;
-    const char *drop = getenv("STG_FX16_TEST_DROP_FILL");
-    b.drop_fill = (drop && drop[0] == '1') ? 1 : 0;
-    launch_k(k_dslash_fx2_staged<EPI>, grid, kFxCons, kFxSmem, s, pdl, b);
+    launch_k(k_dslash_fx2_staged<EPI>, grid, kFxCons, kFxSmem, s, pdl, a);
 }
 
 template <int R>

@@ -289,6 +289,20 @@ static bool want_tiled()
     return !(v && v[0] == '0');
 }
 
+// Test hooks of the staged kernel, read here once per handle so that no
+// launch reads the environment: STG_FX16_GRID=n caps its CTA count (every
+// CTA then walks more tiles through its ring); STG_FX16_TEST_DROP_FILL=1
+// withholds one stage fill, so that a bounded wait runs out (the failure-
+// detection test).
+static void read_fx_hooks(LinkField *lf)
+{
+    const char *v = getenv("STG_FX16_GRID");
+    lf->fx_grid_cap = v ? atoi(v) : 0;
+    if (lf->fx_grid_cap < 0) lf->fx_grid_cap = 0;
+    const char *d = getenv("STG_FX16_TEST_DROP_FILL");
+    lf->fx_drop_fill = (d && d[0] == '1') ? 1 : 0;
+}
+
 // ---------------------------------------------------------------------------
 // field packing
 // ---------------------------------------------------------------------------
@@ -399,7 +413,10 @@ stg_status gauge_create(const int dims[4], const double *links_host, int sloppy,
     const int recon_hi = (sloppy == P64) ? recon : 18;
     if (st == STG_OK) st = pack_links(g->geom, ucan, P64, recon_hi, &g->hi, s);
     if (st == STG_OK && sloppy != P64) st = pack_links(g->geom, ucan, sloppy, recon, &g->lo, s);
-    if (st == STG_OK && sloppy == PX16 && recon == 12 && want_tiled()) st = tile_links(g->geom, &g->lo, s);
+    if (st == STG_OK && sloppy == PX16 && recon == 12 && want_tiled()) {
+        st = tile_links(g->geom, &g->lo, s);
+        read_fx_hooks(&g->lo);
+    }
     if (st == STG_OK && (sloppy == P32 || sloppy == PX16) && recon == 12 && want_mtiled())
         st = mtile_links(g->geom, &g->lo, s);
     e = cudaStreamSynchronize(s);

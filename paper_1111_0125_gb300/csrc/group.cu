@@ -86,6 +86,13 @@ extern "C" stg_status stg_dslash_group(int n, const stg_gauge *const *g, const i
             set_error("stg_dslash_group: handles on different devices or with different reconstruction");
             return STG_ERR_INVALID_ARG;
         }
+        // an output that aliases any item's input would be overwritten
+        // while other threads still read it as a neighbour
+        for (int j = 0; j < n; ++j)
+            if (out_dev[k] == in_dev[j]) {
+                set_error("stg_dslash_group: an item's output aliases an item's input");
+                return STG_ERR_INVALID_ARG;
+            }
         GroupItem &t = ga.it[k];
         t.g = gk->geom;
         for (int mu = 0; mu < 4; ++mu) {

@@ -82,6 +82,10 @@ extern "C" stg_status stg_apply_A_dot_noalloc(const stg_gauge *g, double mass, c
         return STG_ERR_UNSUPPORTED;
     }
     const Geom &geo = g->geom;
+    // every EPI_A_DOT launch writes one partial (8 bytes) per thread block
+    // and uses at most ceil(Vh / kBlock) blocks: one site per thread in
+    // k_dslash, two in k_dslash_fx2, and at most one block per 1024-site
+    // tile in the staged FX16 kernel
     const size_t n_blocks = (size_t)(geo.Vh + kBlock - 1) / kBlock;
     const size_t off_partials = 256;  // the counter lives in the first 256 bytes
     const size_t off_tmp = off_partials + round256(n_blocks * sizeof(double));
@@ -94,8 +98,14 @@ extern "C" stg_status stg_apply_A_dot_noalloc(const stg_gauge *g, double mass, c
     }
 
     int prev = -1;
-    cudaGetDevice(&prev);
-    if (prev != g->device) cudaSetDevice(g->device);
+    cudaError_t de = cudaGetDevice(&prev);
+    if (de != cudaSuccess) return cuda_fail(de, "cudaGetDevice");
+    if (prev != g->device) {
+        // the scratch address below is cached per device: it must be looked
+        // up with the handle's device current
+        de = cudaSetDevice(g->device);
+        if (de != cudaSuccess) return cuda_fail(de, "cudaSetDevice(handle device)");
+    }
     unsigned char *base = nullptr;
     stg_status st = scratch_address(g->device, &base);
     cudaStream_t s = (cudaStream_t)stream;
@@ -125,6 +135,9 @@ extern "C" stg_status stg_apply_A_dot_noalloc(const stg_gauge *g, double mass, c
             st = launch_dslash(geo, prec, EPI_A_DOT, L, s);
         }
     }
-    if (prev >= 0 && prev != g->device) cudaSetDevice(prev);
+    if (prev != g->device) {
+        de = cudaSetDevice(prev);
+        if (de != cudaSuccess && st == STG_OK) st = cuda_fail(de, "cudaSetDevice(restore)");
+    }
     return st;
 }

@@ -60,6 +60,11 @@ struct LinkField {
     size_t tiled_parity_bytes = 0;
     char *mtiled = nullptr; // 12-real FP32 / FX16: tile-major copy (kMTile)
     size_t mtiled_parity_bytes = 0, mtile_bytes = 0;
+    // test hooks of the staged FX16 kernel, read once when the handle is
+    // created (STG_FX16_GRID, STG_FX16_TEST_DROP_FILL): a cap on its CTA
+    // count (0 = none) and the withheld fill of the failure-detection test
+    int fx_grid_cap = 0;
+    int fx_drop_fill = 0;
     const char *blk(int parity, int mu) const { return base + (size_t)(parity * 4 + mu) * blk_bytes; }
 };
 
@@ -171,6 +176,7 @@ struct DslashArgs {
     const char *lf[4];  // forward link blocks  (parity p,   mu)
     const char *lb[4];  // backward link blocks (parity 1-p, mu)
     const char *lt;     // tile-major links of output parity p (FX16 / 12), or null
+    int grid_cap;       // staged kernel: at most this many CTAs (0 = one per SM)
     int drop_fill;      // tests only: the staged kernel withholds the fill of
                         // its second tile's first stage, so that bounded
                         // wait runs out

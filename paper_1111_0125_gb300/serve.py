@@ -13,8 +13,15 @@ lattices overlap on the device.
 Admission is by an HBM budget: a gauge field is uploaded (at most
 `max_resident` at a time, least recently used idle one evicted) and a
 session created only while the budget allows; otherwise the request waits
-until memory frees.  Latency is measured per request from its arrival to the
-moment its solution is back in host memory.
+until memory frees.  The count charges a gauge field with the library's
+resident bytes for its handle (FP64 and sloppy links, tile-major copies,
+workspace scalars) and a session with its batch state plus the source and
+solution buffers of every slot, so everything a request causes on the device
+is counted before it is admitted and released when its session closes.
+`peak_used` is the largest count seen; `peak_measured` the largest device
+usage measured during the run (live torch allocations of the engine plus the
+library's bytes of every live handle and session).  Latency is measured per
+request from its arrival to the moment its solution is back in host memory.
 
 With `priority_by_size`, sessions of smaller lattices run on higher-priority
 CUDA streams, so their short kernels are scheduled ahead of the long
@@ -72,6 +79,13 @@ def gauge_bytes(dims, sloppy: int = STG_FP32, recon: int = 12) -> int:
     return stg_gauge_bytes(dims, sloppy, recon) + 4096
 
 
+def session_bytes(gauge, slots: int, sloppy: int) -> int:
+    """Device bytes of one batch session: the library's count of its state
+    plus a complex128 source and solution buffer (48 bytes per site each)
+    for every slot."""
+    return stg_batch_bytes(gauge.handle, slots, sloppy) + 2 * slots * gauge.vh * 48
+
+
 class _Session:
     """One batch session on one resident gauge field, driven by a thread."""
 
@@ -83,8 +97,10 @@ class _Session:
         params.sloppy = engine.sloppy
         params.check_every = engine.chunk
         self.handle = stg_batch_create(entry.gauge.handle, engine.slots, params, self.stream)
-        self.bytes = stg_batch_bytes(entry.gauge.handle, engine.slots, engine.sloppy)
+        self.lib_bytes = stg_batch_bytes(entry.gauge.handle, engine.slots, engine.sloppy)
         self.vh = entry.gauge.vh
+        # batch state plus one source and one solution buffer per slot
+        self.bytes = session_bytes(entry.gauge, engine.slots, engine.sloppy)
         self.device = device
         self.busy = {}            # slot -> (request, source buffer, solution buffer)
         self.inbox = collections.deque()
@@ -120,6 +136,7 @@ class _Session:
             src = torch.empty((self.vh, 3), dtype=torch.complex128, device=self.device)
             src.copy_(host, non_blocking=True)
             x = torch.zeros_like(src)
+        self.engine._sample_memory()
         slot = stg_batch_add(self.handle, src, x, req.mass, req.tol)
         self.busy[slot] = (req, src, x)
 
@@ -186,6 +203,9 @@ class ServeEngine:
         # higher (more negative) per distinct larger volume
         self._prio = {v: -(len(vols) - 1 - k) for k, v in enumerate(vols)}
         self.used = 0.0
+        self.peak_used = 0.0
+        self.peak_measured = 0.0
+        self._alloc_base = torch.cuda.memory_allocated(device)
         self.resident: dict = {}
         self.results: list = []
         self.lock = threading.Lock()
@@ -203,6 +223,23 @@ class ServeEngine:
 
     def _wake(self):
         self.event.set()
+
+    def _lib_bytes(self) -> int:
+        n = 0
+        for e in list(self.resident.values()):
+            n += e.bytes
+            n += sum(s.lib_bytes for s in list(e.sessions))
+        return n
+
+    def _sample_memory(self):
+        """Device bytes in use now: the engine's live torch tensors (request
+        buffers) plus the library's bytes of every live handle and session."""
+        live = torch.cuda.memory_allocated(self.device) - self._alloc_base
+        m = live + self._lib_bytes()
+        if m > self.peak_measured:
+            self.peak_measured = float(m)
+        if self.used > self.peak_used:
+            self.peak_used = float(self.used)
 
     # -- placement ----------------------------------------------------------
     def _gauge(self, key):
@@ -222,6 +259,7 @@ class ServeEngine:
         e = _GaugeEntry(key, g, need, [], time.perf_counter())
         self.resident[key] = e
         self.used += need
+        self._sample_memory()
         return e
 
     def _evict(self, e):
@@ -242,8 +280,7 @@ class ServeEngine:
             min(open_s, key=lambda s: s.load()).submit(req)
             return True
         if len(e.sessions) < self.max_sessions:
-            need = stg_batch_bytes(e.gauge.handle, self.slots, self.sloppy) + \
-                2 * self.slots * e.gauge.vh * 48
+            need = session_bytes(e.gauge, self.slots, self.sloppy)
             if self.used + need <= self.budget:
                 prio = 0
                 if self.priority_by_size:
@@ -251,6 +288,7 @@ class ServeEngine:
                 s = _Session(self, e, self.device, prio)
                 self.used += s.bytes
                 e.sessions.append(s)
+                self._sample_memory()
                 s.submit(req)
                 return True
         return False
@@ -278,6 +316,7 @@ class ServeEngine:
                 if not self._place(r):
                     still.append(r)
             pending = still
+            self._sample_memory()
             with self.lock:
                 finished = len(self.results)
             if finished == n:

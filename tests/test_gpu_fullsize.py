@@ -104,3 +104,30 @@ def test_c2_mixed_vs_fp64_16x32():
     # by bench.py, not pinned: it depends on the system's iteration count.)
     assert sm["sloppy_iters"] == sm["iters"] and sd["sloppy_iters"] == 0
     assert 0 < sm["updates"] < sm["iters"]
+
+
+@pytest.mark.parametrize("prec", [stg.STG_FX16, stg.STG_FP32])
+def test_dot_reduction_against_exact_sum_32x64(prec):
+    """d^dag A d of stg_apply_A_dot at 32^3 x 64 (the reduction of the CG's
+    alpha, and the same grid_sum_ff code as its |r|^2) against the exact sum.
+    Per site the kernel forms Re d^dag q in FP32 from the values as stored;
+    sites are summed in compensated FP32 pairs and the grid total in FP64.
+    Products of two FP32 values are exact in FP64, so math.fsum over them is
+    the exactly rounded sum.  The per-site FP32 rounding (relative 2^-24 per
+    term, random in sign) leaves about 2^-24 / sqrt(n) of the sum of |terms|
+    over n = 3 Vh terms; the bound asserted is 2^-30 of that sum."""
+    import math
+    dims, mass = (32, 32, 32, 64), 0.005
+    U = _gauge(dims, 0.6)
+    chi = gen.source(dims, seed=1)
+    with stg.Gauge(dims, U, sloppy=prec, recon=12) as g:
+        f = g.pack(torch.from_numpy(chi).cuda(), prec)
+        out, dot = g.apply_A_dot(f, mass, prec)
+        d = g.unpack(f, prec).cpu().numpy()
+        q = g.unpack(out, prec).cpu().numpy()
+        got = dot.item()
+    prods = np.concatenate([(d.real * q.real).ravel(), (d.imag * q.imag).ravel()])
+    exact = math.fsum(prods.tolist())
+    scale = math.fsum(np.abs(prods).tolist())
+    assert exact > 0
+    assert abs(got - exact) <= 2.0 ** -30 * scale, (got, exact, (got - exact) / scale)

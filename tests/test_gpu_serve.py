@@ -1,6 +1,7 @@
 """Serving loop: requests of several lattices and gauge fields, more requests
 than batch slots (so systems join running batches), checked against the same
-requests solved alone and against the oracle's A."""
+requests solved alone and against the oracle's A; the HBM budget checked
+against measured device usage."""
 import numpy as np
 import pytest
 import torch
@@ -8,7 +9,7 @@ import torch
 import gen
 import oracle
 import paper_1111_0125_gb300 as stg
-from paper_1111_0125_gb300.serve import Request, ServeEngine
+from paper_1111_0125_gb300.serve import Request, ServeEngine, gauge_bytes, session_bytes
 
 pytestmark = pytest.mark.gpu
 
@@ -85,6 +86,60 @@ def test_one_resident_field_evicts_and_waits():
     finally:
         eng.close()
     _check(results, reqs, gauges, sources)
+
+
+def test_small_budget_holds_on_the_device():
+    """An HBM budget with room for one gauge field and one session of the
+    largest lattice: requests queue until memory frees, every one is served,
+    and neither the engine's count nor the device usage measured during the
+    run (its live torch buffers plus the library's bytes of every live handle
+    and session) ever exceeds the budget."""
+    gauges, sources = _tables()
+    biggest = max(gauges, key=lambda k: int(np.prod(gauges[k][0])))
+    dims, links = gauges[biggest]
+    with stg.Gauge(dims, links, sloppy=stg.STG_FP32, recon=12) as g:
+        need = gauge_bytes(dims, stg.STG_FP32, 12) + session_bytes(g, 2, stg.STG_FP32)
+    budget = need + 4096
+    reqs = _requests(12, seed=8)
+    eng = ServeEngine(gauges, sources, hbm_budget=budget, slots=2, max_sessions_per_gauge=1,
+                      keep_solutions=True)
+    try:
+        results = eng.run(reqs, realtime=False)
+        assert 0 < eng.peak_used <= budget
+        assert 0 < eng.peak_measured <= budget
+    finally:
+        eng.close()
+    _check(results, reqs, gauges, sources)
+
+
+def _free_bytes():
+    torch.cuda.synchronize()
+    return torch.cuda.mem_get_info()[0]
+
+
+@pytest.mark.parametrize("sloppy", [stg.STG_FP32, stg.STG_FX16])
+def test_library_byte_counts_match_device_memory(sloppy):
+    """The byte counts the budget relies on (stg_gauge_bytes, stg_batch_bytes)
+    against the drop of the device's free memory when the handle and the
+    session are created (each allocation rounded up to 2 MiB pages)."""
+    dims = (16, 16, 16, 32)
+    U = gen.gauge_field(dims, "exp", seed=1, eps=0.5)
+    with stg.Gauge(dims, U, sloppy=sloppy, recon=12) as warm:   # loads the kernels once
+        b = stg.stg_batch_create(warm.handle, 4, warm.params())
+        stg.stg_batch_destroy(b)
+    page = 2 << 20
+    f0 = _free_bytes()
+    with stg.Gauge(dims, U, sloppy=sloppy, recon=12) as g:
+        f1 = _free_bytes()
+        want = stg.stg_gauge_bytes(dims, sloppy, 12)
+        assert want - page <= f0 - f1 <= want + 4 * page, (f0 - f1, want)
+        b = stg.stg_batch_create(g.handle, 4, g.params())
+        try:
+            f2 = _free_bytes()
+            want_b = stg.stg_batch_bytes(g.handle, 4, sloppy)
+            assert want_b - page <= f1 - f2 <= want_b + 14 * page, (f1 - f2, want_b)
+        finally:
+            stg.stg_batch_destroy(b)
 
 
 def test_batch_session_join_while_running():

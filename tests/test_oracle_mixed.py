@@ -67,3 +67,37 @@ def test_refinement_variant_converges_and_restarts_cost_iterations():
     kappa = (mass ** 2 + 64) / mass ** 2
     assert rel(xr, xe) <= 2 * kappa * tol
     assert ie["iters"] <= ir["iters"]
+
+
+def _eq6_direction_error(o):
+    """Relative distance between the emulation's new search direction at its
+    first reliable update and Eq. 6's d = r^ + (|r|^2 / delta_old) d, formed
+    here from the new true residual r = b - A x (x as the oracle left it,
+    A re-applied) and the oracle's d before the update; also the iterated-
+    vs-true gap that makes a plain-CG beta distinguishable."""
+    dims, mass = (4, 4, 4, 8), 0.02
+    U = gen.gauge_field(dims, "exp", seed=5, eps=0.5)
+    b = gen.source(dims, seed=1)
+    _, info = o.cg_mixed(dims, U, mass, b, tol=1e-10, delta=1e-3, snapshot=True)
+    fu = info["first_update"]
+    r = b - o.apply_A(dims, U, mass, fu["x"])
+    r_hat = r.astype(np.complex64)                       # group-wise update: r^ = r
+    true2 = float(np.vdot(r, r).real)
+    want = (r_hat.astype(np.complex128) + (true2 / fu["rho_prev"]) * fu["d_old"])
+    want = want.astype(np.complex64)
+    err = float(np.linalg.norm(fu["d_new"] - want) / np.linalg.norm(want))
+    gap = abs(fu["rho_iter"] - true2) / true2
+    same_r = bool(np.array_equal(fu["r_hat"].astype(np.complex64), r_hat))
+    return err, gap, same_r
+
+
+def test_eq6_search_direction_at_the_update():
+    """Eq. 6 (reading: r is the new true residual, beta = |r|^2 / delta_old,
+    d kept): the oracle's first corrected direction is that formula applied
+    to its own outputs.  The iterated |r^|^2 differs from the true |r|^2 by
+    about 1e-3 here, so a plain CG beta (|r^|^2 / delta_old) would miss by
+    that much."""
+    err, gap, same_r = _eq6_direction_error(oracle)
+    assert same_r
+    assert gap > 1e-4
+    assert err < 1e-6 * gap

@@ -3,7 +3,7 @@
 Each case below plants one mistake in a copy of oracle/stg_oracle.c -- a
 dropped direction, a wrong sign, a missing dagger, a transposed link, a wrong
 staggered phase or boundary, a wrong neighbour or checkerboard index, a wrong
-CG coefficient -- compiles the copy, and requires at least one pin check to
+CG coefficient, a plain-CG beta at the mixed solver's update -- compiles the copy, and requires at least one pin check to
 fail; the unchanged oracle must pass all of them.  A reversed phase order is
 a valid convention with the same spectrum, so only the explicit single-site
 hop sum catches that one.  The mistakes live only in temporary copies on the
@@ -19,6 +19,7 @@ import pytest
 import gen
 from lattice_util import (dense_A, free_eigenvalue, momentum, plane_wave, rel,
                           site_coords, transform_field, transform_gauge)
+from test_oracle_mixed import _eq6_direction_error
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "stg_oracle.c")
@@ -48,6 +49,8 @@ MUTANTS = {
                          "double beta = delta_old / delta_new;"),
     "cg_alpha_without_A": ("double alpha = delta_new / dq;",
                            "double alpha = delta_new / re_dot(d, d, n);"),
+    "mixed_beta_from_iterated_residual": ("mult = refine ? 0.0 : true2 / rho_prev;",
+                                          "mult = refine ? 0.0 : rho / rho_prev;"),
 }
 
 
@@ -145,7 +148,12 @@ def _pin_failures(o):
                 return False
         return True
 
+    def eq6_direction():
+        err, gap, same_r = _eq6_direction_error(o)
+        return same_r and gap > 1e-4 and err < 1e-6 * gap
+
     for name, fn in [("free_field", free_field), ("hop_sum", hop_sum),
+                     ("eq6_direction", eq6_direction),
                      ("anti_hermitian", anti_hermitian),
                      ("covariance", covariance), ("dense_solve", dense_solve),
                      ("one_iteration", one_iteration)]:
