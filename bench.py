@@ -68,7 +68,12 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 CG comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--kernels-only", action="store_true")
+    ap.add_argument("--kernels-only", action="store_true",
+                    help="launch the Dslash kernels alone, --reps times (for ncu); with "
+                         "--workload c4 the multi-system Dslash of the 16 systems")
+    ap.add_argument("--kernels", default="all", choices=["all", "sloppy", "f64"],
+                    help="--kernels-only: the sloppy-precision Dslash and A, the FP64 Dslash, "
+                         "or both")
     ap.add_argument("--workload", default="c3", choices=["c3", "c4", "c5"],
                     help="c3: 32^3x64 single solve (default); c4: 24^3x48, 16 systems "
                          "batched; c5: Poisson stream of solve requests (serving)")
@@ -79,6 +84,11 @@ def parse():
     ap.add_argument("--rate", type=float, default=0.0,
                     help="c5: offered rate at --load in requests/s (0: --load x saturation)")
     ap.add_argument("--sessions", type=int, default=2, help="c5: batch sessions per gauge field")
+    ap.add_argument("--group-max-vh", type=int, default=20736,
+                    help="c5: lattices of at most this many sites per parity are served by "
+                         "lattice-group sessions (0: every lattice by per-field batch sessions)")
+    ap.add_argument("--group-slots", type=int, default=8, help="c5: systems per lattice group")
+    ap.add_argument("--max-groups", type=int, default=2, help="c5: lattice-group sessions")
     ap.add_argument("--chunk", type=int, default=16,
                     help="c5: CG iterations per session step (larger chunks for small "
                          "lattices measured worse: slots refill later)")
@@ -458,8 +468,9 @@ def c4_measure(args, steps, warmup, one_by_one_reps=1):
     s1.synchronize()
     t_m = s0.elapsed_time(s1) / 20
     L, S = LINK_BYTES[(c4_sloppy, args.recon)], FIELD_BYTES[c4_sloppy]
-    # links once per NB x TPS systems (register-fed), once for all (staged, tb = 0)
-    link_passes = 1 if tb == 0 else -(-n // (nb * tb))
+    # links once per NB x TPS systems (register-fed), once for all (staged,
+    # tb = 0, or staged with two sites per thread, tb = -1)
+    link_passes = 1 if tb <= 0 else -(-n // (nb * tb))
     nbytes = vh * (8 * L * link_passes + 2 * S * n)
     peak, src_ = measured_hbm()
     achieved = nbytes / (t_m / 1000.0) / 1e9
@@ -475,7 +486,9 @@ def c4_measure(args, steps, warmup, one_by_one_reps=1):
         "true_res_max": max(s_["true_res"] for s_ in st),
         "iters_one_by_one": [s_["iters"] for s_ in single],
         "mrhs_dslash": {"rhs_block": nb, "threads_per_site": tb,
-                        "kernel": "k_dslash_ms (staged)" if tb == 0 else "k_dslash_m",
+                        "kernel": ("k_dslash_ms (staged)" if tb == 0 else
+                                   "k_dslash_msp (staged, two sites per thread)" if tb == -1
+                                   else "k_dslash_m"),
                         "launch_ms": t_m,
                         "algorithmic_bytes_per_launch": nbytes,
                         "bytes_per_site_per_system": nbytes / vh / n,
@@ -486,7 +499,38 @@ def c4_measure(args, steps, warmup, one_by_one_reps=1):
     }
 
 
+def c4_kernels_only(args):
+    """The multi-system Dslash of the 16 C4 systems alone, --reps launches
+    (the autotuner's shape, or STG_MRHS_SHAPE), for ncu."""
+    import numpy as np
+    import torch
+
+    import gen
+    import paper_1111_0125_gb300 as stg
+    dims, n = (24, 24, 24, 48), args.nrhs
+    torch.cuda.set_device(0)
+    U = gen.gauge_field(dims, "exp", seed=0, eps=0.5)
+    bs = gen.source(dims, seed=1, nrhs=n)
+    sloppy = {"f32": stg.STG_FP32, "fx16": stg.STG_FX16, "f16": stg.STG_FP16}[args.c4_sloppy]
+    with stg.Gauge(dims, U, sloppy=sloppy, recon=args.recon) as g:
+        src = torch.from_numpy(np.ascontiguousarray(bs)).cuda()
+        fb = stg.stg_field_bytes(g.handle, sloppy)
+        fin = torch.empty(n * fb, dtype=torch.uint8, device="cuda")
+        for k in range(n):
+            stg.stg_pack_field(g.handle, sloppy, src[k], fin[k * fb:(k + 1) * fb])
+        fout = torch.empty_like(fin)
+        for _ in range(args.reps):
+            stg.stg_dslash_mrhs(g.handle, 1, n, fin, fout, sloppy)
+        torch.cuda.synchronize()
+        nb, tb = stg.stg_mrhs_tuning(g.handle, sloppy, n)
+    print(json.dumps({"kernels_only": True, "workload": "c4", "reps": args.reps,
+                      "sloppy_storage": args.c4_sloppy, "rhs_block": nb, "threads_per_site": tb}))
+
+
 def run_c4(args):
+    if args.kernels_only:
+        c4_kernels_only(args)
+        return
     r = c4_measure(args, args.steps, args.warmup, one_by_one_reps=1)
     print(json.dumps({
         "metric": METRIC, "workload": "c4: " + r["workload"],
@@ -547,7 +591,9 @@ def c5_measure(args, n_requests, sat_requests, loads, warm_requests=64):
     eng = ServeEngine(gauges, sources, hbm_budget=120e9, slots=args.slots,
                       max_sessions_per_gauge=args.sessions,
                       max_resident=8, sloppy=sloppy, recon=args.recon,
-                      priority_by_size=not args.no_priority, chunk=args.chunk)
+                      priority_by_size=not args.no_priority, chunk=args.chunk,
+                      group_max_vh=args.group_max_vh, group_slots=args.group_slots,
+                      max_groups=args.max_groups)
     try:
         eng.run(c5_requests(warm_requests, None, seed=7), realtime=False)   # warm-up, tuning
         sat_res = eng.run(c5_requests(sat_requests, None), realtime=False)
@@ -592,7 +638,9 @@ def c5_measure(args, n_requests, sat_requests, loads, warm_requests=64):
                    "mass": "log-uniform [0.005, 0.1]", "tol": "1e-8 or 1e-10",
                    "slots_per_session": args.slots, "sessions_per_gauge": args.sessions,
                    "stream_priority_by_lattice_size": not args.no_priority,
-                   "iterations_per_step": args.chunk, "sloppy_storage": c5_sloppy},
+                   "iterations_per_step": args.chunk, "sloppy_storage": c5_sloppy,
+                   "lattice_groups": {"max_vh": args.group_max_vh, "slots": args.group_slots,
+                                      "sessions": args.max_groups}},
         "clocks": ck,
     }
 
@@ -683,11 +731,13 @@ def main():
         out = g.new_field(sloppy)
         f64 = g.pack(b, stg.STG_FP64)
         o64 = g.new_field(stg.STG_FP64)
-        for _ in range(args.reps):
-            g.dslash(f, 1, sloppy, out=out)
-            g.apply_A(f, args.mass, sloppy, out=out)
-        for _ in range(args.reps):
-            g.dslash(f64, 1, stg.STG_FP64, out=o64)
+        if args.kernels in ("all", "sloppy"):
+            for _ in range(args.reps):
+                g.dslash(f, 1, sloppy, out=out)
+                g.apply_A(f, args.mass, sloppy, out=out)
+        if args.kernels in ("all", "f64"):
+            for _ in range(args.reps):
+                g.dslash(f64, 1, stg.STG_FP64, out=o64)
         torch.cuda.synchronize()
         if rank == 0:
             print(json.dumps({"kernels_only": True, "lattice": dims, "reps": args.reps}))

@@ -339,13 +339,54 @@ stg_status stg_batch_step(stg_batch *b, int max_done, int *done_slots, int *done
                           stg_cg_stats *done_stats, int *n_done, int *n_active);
 size_t stg_batch_bytes(const stg_gauge *g, int max_systems, stg_prec sloppy);
 
+/*
+ * Lattice-group session: systems on different lattices (each on its own
+ * gauge handle, of any size up to max_vh sites per parity) iterate the CG of
+ * Fig. 1 in lock-step, one grid per kernel for all of them: t_k = D_oe d_k,
+ * q_k = m_k^2 d_k - D_eo t_k with d_k^dag q_k (Eq. 3), the update with
+ * |r_k|^2, and d_k = r_k + beta_k d_k -- four launches per iteration for the
+ * whole group, captured once in a CUDA graph and replayed.  Each system
+ * keeps its own alpha, beta and stop flag and leaves when it converges;
+ * between chunks the session performs the Sec. 3.2 reliable and group-wise
+ * updates (x_k += y_k, r_k = b_k - A_k x_k in FP64 with the system's own
+ * handle) and the Eq. 6 restart, as stg_batch_step does.  Small lattices
+ * fill little of the GPU one launch at a time; a group fills it.
+ *   stg_lgroup_create: max_systems 1..16; max_vh the largest Vh a slot will
+ *     hold; sloppy the inner storage precision and recon (12 / 18) of the
+ *     handles it will take; params as for stg_batch_create (NULL = RELIABLE
+ *     with the precision's default delta).  Allocates its buffers on the
+ *     current device.
+ *   stg_lgroup_add: the handle must be on the session's device, hold links
+ *     in `sloppy` with reconstruction `recon`, and have Vh <= max_vh (else
+ *     STG_ERR_INVALID_ARG / STG_ERR_UNSUPPORTED); src_dev / x_dev canonical
+ *     complex128 [Vh][3] device fields owned by the caller until the system
+ *     is reported done, x_dev holding x0 on entry.  The handle must outlive
+ *     the system's stay.  Synchronises the session stream.
+ *   stg_lgroup_step / stg_lgroup_bytes / stg_lgroup_destroy: as for the
+ *     batch session.
+ * The paper solves one lattice at a time; this is a serving-layer form of
+ * the same iteration.
+ */
+typedef struct stg_lgroup stg_lgroup;
+stg_status stg_lgroup_create(int max_systems, long max_vh, stg_prec sloppy, int recon,
+                             const stg_cg_params *params, stg_stream_t stream, stg_lgroup **out);
+stg_status stg_lgroup_destroy(stg_lgroup *b);
+stg_status stg_lgroup_add(stg_lgroup *b, const stg_gauge *g, const double *src_dev, double *x_dev,
+                          double mass, double tol, int *slot);
+stg_status stg_lgroup_step(stg_lgroup *b, int max_done, int *done_slots, int *done_status,
+                           stg_cg_stats *done_stats, int *n_done, int *n_active);
+size_t stg_lgroup_bytes(int max_systems, long max_vh, stg_prec sloppy);
+
 /* The autotuner's choice (rhs_block = NB systems per thread and block,
  * threads_per_site = TPS) for this handle's lattice, `prec` and nrhs;
  * threads_per_site = 0 names the staged kernel (12-real FP32 / FX16 links
  * streamed through shared memory, one link load per site for all systems,
- * NB systems per thread and pass).  STG_ERR_INVALID_ARG if not tuned yet.
- * The environment variable STG_MRHS_SHAPE=<k> forces shape k (0-8:
- * register-fed (NB, TPS); 9-11: staged NB = 2, 4, 8) where it applies. */
+ * NB systems per thread and pass), threads_per_site = -1 its FX16 / 12-real
+ * form with two sites per thread on packed FP32x2 arithmetic.
+ * STG_ERR_INVALID_ARG if not tuned yet.  The environment variable
+ * STG_MRHS_SHAPE=<k> forces shape k (0-8: register-fed (NB, TPS); 9-11:
+ * staged NB = 2, 4, 8; 12-13: staged two sites per thread, NB = 2, 4) where
+ * it applies. */
 stg_status stg_mrhs_tuning(const stg_gauge *g, stg_prec prec, int nrhs, int *rhs_block,
                            int *threads_per_site);
 

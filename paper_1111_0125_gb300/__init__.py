@@ -97,6 +97,11 @@ def _load():
         "stg_batch_add": (i, [p, p, p, d, d, p]),
         "stg_batch_step": (i, [p, i, p, p, p, p, p]),
         "stg_batch_bytes": (sz, [p, i, i]),
+        "stg_lgroup_create": (i, [i, ctypes.c_long, i, i, p, p, p]),
+        "stg_lgroup_destroy": (i, [p]),
+        "stg_lgroup_add": (i, [p, p, p, p, d, d, p]),
+        "stg_lgroup_step": (i, [p, i, p, p, p, p, p]),
+        "stg_lgroup_bytes": (sz, [i, ctypes.c_long, i]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -306,6 +311,43 @@ def stg_batch_step(batch: int, max_done: int = 64):
     _check(lib.stg_batch_step(batch, int(max_done), slots, status, stats, ctypes.byref(n_done),
                               ctypes.byref(n_act)), "stg_batch_step")
     return ([(slots[k], status[k], stats[k].as_dict()) for k in range(n_done.value)], n_act.value)
+
+
+def stg_lgroup_create(max_systems: int, max_vh: int, sloppy: int, recon: int = 12, params=None,
+                      stream=None) -> int:
+    """Lattice-group session: systems on different lattices in lock-step."""
+    b = ctypes.c_void_p()
+    pp = ctypes.byref(params) if params is not None else None
+    _check(lib.stg_lgroup_create(int(max_systems), int(max_vh), int(sloppy), int(recon), pp,
+                                 _stream(stream), ctypes.byref(b)), "stg_lgroup_create")
+    return b.value
+
+
+def stg_lgroup_destroy(group: int) -> None:
+    lib.stg_lgroup_destroy(group)
+
+
+def stg_lgroup_add(group: int, handle: int, src_dev, x_dev, mass: float, tol: float) -> int:
+    slot = ctypes.c_int()
+    _check(lib.stg_lgroup_add(group, handle, _ptr(src_dev), _ptr(x_dev), float(mass), float(tol),
+                              ctypes.byref(slot)), "stg_lgroup_add")
+    return slot.value
+
+
+def stg_lgroup_step(group: int, max_done: int = 16):
+    """One chunk for every system of the group; returns ([(slot, status,
+    stats), ...] for finished systems, systems still present)."""
+    slots = (ctypes.c_int * max(1, max_done))()
+    status = (ctypes.c_int * max(1, max_done))()
+    stats = (stg_cg_stats * max(1, max_done))()
+    n_done, n_act = ctypes.c_int(), ctypes.c_int()
+    _check(lib.stg_lgroup_step(group, int(max_done), slots, status, stats, ctypes.byref(n_done),
+                               ctypes.byref(n_act)), "stg_lgroup_step")
+    return ([(slots[k], status[k], stats[k].as_dict()) for k in range(n_done.value)], n_act.value)
+
+
+def stg_lgroup_bytes(max_systems: int, max_vh: int, sloppy: int) -> int:
+    return int(lib.stg_lgroup_bytes(int(max_systems), int(max_vh), int(sloppy)))
 
 
 def stg_gauge_bytes(dims, sloppy: int, recon: int) -> int:

@@ -10,182 +10,15 @@
 // __fadd2_rn, __fmul2_rn) for both sites.  Loads of A and B are separate and
 // stay coalesced across the warp.
 //
-// Signs are never negated in the inner loops: each colour keeps positive and
-// negative real / imaginary accumulators (Pr, Nr, Pi, Ni) and D chi =
-// (Pr - Nr) + i (Pi - Ni) once at the end.  Links are integer-valued floats
-// (32767 U); the sum is scaled by 1/32767 at the end, and the 12-real row 2
-// c = r0 x r1 enters the products with the factor s / 32767 (s the folded
-// phase), i.e. U_2b = (s / 32767) conj(c_b).
-#include "stg_internal.h"
+// The packed arithmetic (decode, 12-real reconstruction, mat-vecs, FX16
+// encode) is in fx16_pair.cuh.
+#include "fx16_pair.cuh"
 
 #ifndef STG_FX2_MINBLOCKS
 #define STG_FX2_MINBLOCKS 2
 #endif
 
 namespace stg {
-
-typedef float2 f2;
-
-__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ f2 mul2(f2 a, f2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ f2 add2(f2 a, f2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ f2 sub2(f2 a, f2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
-
-// biased fixed-point decode (see fx_lo / fx_hi): 1.5 * 2^23 + u, then the
-// subtraction of 1.5 * 2^23 + 32768 happens once for both sites
-__device__ __forceinline__ float fxb_lo(unsigned w) { return __int_as_float((int)__byte_perm(w, 0x4B40u, 0x5410)); }
-__device__ __forceinline__ float fxb_hi(unsigned w) { return __int_as_float((int)__byte_perm(w, 0x4B40u, 0x5432)); }
-__device__ __forceinline__ f2 unbias(float a, float b)
-{
-    return add2(make_float2(a, b), make_float2(-12615680.f, -12615680.f));
-}
-
-struct Mat3x2 {
-    f2 r[3][3], i[3][3];
-};
-struct Vec3x2 {
-    f2 r[3], i[3];
-};
-
-__device__ __forceinline__ void set2(Mat3x2 &u, int k, unsigned wa, unsigned wb)
-{
-    u.r[k / 3][k % 3] = unbias(fxb_lo(wa), fxb_lo(wb));
-    u.i[k / 3][k % 3] = unbias(fxb_hi(wa), fxb_hi(wb));
-}
-
-// 12-real: row 2 is c = r0 x r1 (no conjugate, no sign, 32767^2 scale);
-// a / b hold rows 0-1 entries 0-3 of sites A / B, c / d entries 4-5
-__device__ __forceinline__ void decode12(const uint4 &a, const uint4 &b, const uint2 &c, const uint2 &d,
-                                         Mat3x2 &u)
-{
-    set2(u, 0, a.x, b.x);
-    set2(u, 1, a.y, b.y);
-    set2(u, 2, a.z, b.z);
-    set2(u, 3, a.w, b.w);
-    set2(u, 4, c.x, d.x);
-    set2(u, 5, c.y, d.y);
-#pragma unroll
-    for (int a2 = 0; a2 < 3; ++a2) {
-        const int b2 = (a2 + 1) % 3, c2 = (a2 + 2) % 3;
-        // c = r0_b r1_c - r0_c r1_b as one FMA chain per part (the negated
-        // operands cost no instruction)
-        const f2 nrc = make_float2(-u.r[0][c2].x, -u.r[0][c2].y);
-        const f2 nib = make_float2(-u.i[0][b2].x, -u.i[0][b2].y);
-        const f2 nic = make_float2(-u.i[0][c2].x, -u.i[0][c2].y);
-        f2 re = mul2(u.r[0][b2], u.r[1][c2]);
-        re = fma2(nib, u.i[1][c2], re);
-        re = fma2(nrc, u.r[1][b2], re);
-        re = fma2(u.i[0][c2], u.i[1][b2], re);
-        f2 im = mul2(u.r[0][b2], u.i[1][c2]);
-        im = fma2(u.i[0][b2], u.r[1][c2], im);
-        im = fma2(nrc, u.i[1][b2], im);
-        im = fma2(nic, u.r[1][b2], im);
-        u.r[2][a2] = re;
-        u.i[2][a2] = im;
-    }
-}
-
-// link of site A (index sa) and site B (index sb) of one (parity, mu) block
-template <int R>
-__device__ __forceinline__ void load_link2(const char *blk, int vh, int sa, int sb, Mat3x2 &u)
-{
-    const uint4 *p = reinterpret_cast<const uint4 *>(blk);
-    const uint4 a = ld_stream(p + sa), b = ld_stream(p + sb);
-    if (R == 18) {
-        set2(u, 0, a.x, b.x);
-        set2(u, 1, a.y, b.y);
-        set2(u, 2, a.z, b.z);
-        set2(u, 3, a.w, b.w);
-        const uint4 c = ld_stream(p + (size_t)vh + sa), d = ld_stream(p + (size_t)vh + sb);
-        set2(u, 4, c.x, d.x);
-        set2(u, 5, c.y, d.y);
-        set2(u, 6, c.z, d.z);
-        set2(u, 7, c.w, d.w);
-        const unsigned *q = reinterpret_cast<const unsigned *>(p + (size_t)2 * vh);
-        set2(u, 8, ld_stream(q + sa), ld_stream(q + sb));
-    } else {
-        const uint2 *q = reinterpret_cast<const uint2 *>(p + (size_t)vh);
-        decode12(a, b, ld_stream(q + sa), ld_stream(q + sb), u);
-    }
-}
-
-__device__ __forceinline__ void load_field2(const void *f, int sa, int sb, Vec3x2 &v)
-{
-    const uint4 *p = static_cast<const uint4 *>(f);
-    const uint4 a = __ldg(p + sa), b = __ldg(p + sb);
-    const f2 sc = make_float2(__uint_as_float(a.w), __uint_as_float(b.w));
-    v.r[0] = mul2(unbias(fxb_lo(a.x), fxb_lo(b.x)), sc);
-    v.i[0] = mul2(unbias(fxb_hi(a.x), fxb_hi(b.x)), sc);
-    v.r[1] = mul2(unbias(fxb_lo(a.y), fxb_lo(b.y)), sc);
-    v.i[1] = mul2(unbias(fxb_hi(a.y), fxb_hi(b.y)), sc);
-    v.r[2] = mul2(unbias(fxb_lo(a.z), fxb_lo(b.z)), sc);
-    v.i[2] = mul2(unbias(fxb_hi(a.z), fxb_hi(b.z)), sc);
-}
-
-struct Acc2 {
-    f2 pr[3], nr[3], pi[3], ni[3];
-};
-
-// acc += U v; for 12-real, row 2 of U is s2 conj(c)
-template <int R>
-__device__ __forceinline__ void fwd2(const Mat3x2 &u, const Vec3x2 &v, f2 s2, Acc2 &A)
-{
-    constexpr int nrow = R == 18 ? 3 : 2;
-#pragma unroll
-    for (int a = 0; a < nrow; ++a)
-#pragma unroll
-        for (int b = 0; b < 3; ++b) {
-            A.pr[a] = fma2(u.r[a][b], v.r[b], A.pr[a]);
-            A.nr[a] = fma2(u.i[a][b], v.i[b], A.nr[a]);
-            A.pi[a] = fma2(u.r[a][b], v.i[b], A.pi[a]);
-            A.pi[a] = fma2(u.i[a][b], v.r[b], A.pi[a]);
-        }
-    if (R == 12) {
-        // sum_b conj(c_b) v_b = sum (c.r v.r + c.i v.i) + i sum (c.r v.i - c.i v.r)
-        f2 wr = mul2(u.r[2][0], v.r[0]);
-        f2 wp = mul2(u.r[2][0], v.i[0]);
-        f2 wn = mul2(u.i[2][0], v.r[0]);
-        wr = fma2(u.i[2][0], v.i[0], wr);
-#pragma unroll
-        for (int b = 1; b < 3; ++b) {
-            wr = fma2(u.r[2][b], v.r[b], wr);
-            wr = fma2(u.i[2][b], v.i[b], wr);
-            wp = fma2(u.r[2][b], v.i[b], wp);
-            wn = fma2(u.i[2][b], v.r[b], wn);
-        }
-        A.pr[2] = fma2(s2, wr, A.pr[2]);
-        A.pi[2] = fma2(s2, wp, A.pi[2]);
-        A.ni[2] = fma2(s2, wn, A.ni[2]);
-    }
-}
-
-// acc -= U^dag v; for 12-real, conj(U_2a) = s2 c_a
-template <int R>
-__device__ __forceinline__ void bwd2(const Mat3x2 &u, const Vec3x2 &v, f2 s2, Acc2 &A)
-{
-    constexpr int nrow = R == 18 ? 3 : 2;
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int b = 0; b < nrow; ++b) {
-            // conj(U_ba) v_b = (u.r v.r + u.i v.i) + i (u.r v.i - u.i v.r)
-            A.nr[a] = fma2(u.r[b][a], v.r[b], A.nr[a]);
-            A.nr[a] = fma2(u.i[b][a], v.i[b], A.nr[a]);
-            A.ni[a] = fma2(u.r[b][a], v.i[b], A.ni[a]);
-            A.pi[a] = fma2(u.i[b][a], v.r[b], A.pi[a]);
-        }
-    if (R == 12) {
-        // s2 c_a v_2 = s2 (c.r v.r - c.i v.i) + i s2 (c.r v.i + c.i v.r)
-        const f2 wr = mul2(s2, v.r[2]), wi = mul2(s2, v.i[2]);
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            A.nr[a] = fma2(u.r[2][a], wr, A.nr[a]);
-            A.pr[a] = fma2(u.i[2][a], wi, A.pr[a]);
-            A.ni[a] = fma2(u.r[2][a], wi, A.ni[a]);
-            A.ni[a] = fma2(u.i[2][a], wr, A.ni[a]);
-        }
-    }
-}
 
 // decode one FX16 site record already in registers
 __device__ __forceinline__ Vec3<float> fx_decode(uint4 u)
@@ -196,6 +29,15 @@ __device__ __forceinline__ Vec3<float> fx_decode(uint4 u)
     v.r[1] = fx_lo(u.y) * sc; v.i[1] = fx_hi(u.y) * sc;
     v.r[2] = fx_lo(u.z) * sc; v.i[2] = fx_hi(u.z) * sc;
     return v;
+}
+
+// The packed epilogue over the kernel's output field (epilogue_pair)
+template <int EPI>
+__device__ __forceinline__ f2 epilogue2(const DslashArgs &a, int iA, int iB, bool okA, bool okB,
+                                        const f2 (&dr)[3], const f2 (&di)[3], float m2, uint4 wA,
+                                        uint4 wB)
+{
+    return epilogue_pair<EPI>(a.out, iA, iB, okA, okB, dr, di, m2, wA, wB);
 }
 
 // the scalar epilogue of one site (same arithmetic as k_dslash's); wraw is
@@ -234,6 +76,23 @@ __device__ __forceinline__ float epilogue(const DslashArgs &a, int vh, int i, co
     return dot;
 }
 
+// D chi = (P - N) / 32767 of both sites, negated for the A epilogues, then
+// the packed epilogue
+template <int EPI>
+__device__ __forceinline__ f2 finish_pair(const DslashArgs &a, int iA, int iB, bool okA, bool okB,
+                                          const Acc2 &A, float m2, uint4 wA, uint4 wB)
+{
+    const f2 k = make_float2(LinkPost<PX16>::k, LinkPost<PX16>::k);
+    constexpr bool neg = (EPI == EPI_A || EPI == EPI_A_DOT || EPI == EPI_A_CG);
+    f2 dr[3], di[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        dr[c] = mul2(A.re[c], neg ? neg2(k) : k);
+        di[c] = mul2(A.im[c], neg ? neg2(k) : k);
+    }
+    return epilogue2<EPI>(a, iA, iB, okA, okB, dr, di, m2, wA, wB);
+}
+
 template <int R, int EPI>
 __global__ void __launch_bounds__(kBlock, STG_FX2_MINBLOCKS) k_dslash_fx2(const DslashArgs a)
 {
@@ -260,7 +119,7 @@ __global__ void __launch_bounds__(kBlock, STG_FX2_MINBLOCKS) k_dslash_fx2(const 
         const Site sB = site_of(a.g, jB, a.parity);
         Acc2 A;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) A.pr[c] = A.nr[c] = A.pi[c] = A.ni[c] = make_float2(0.f, 0.f);
+        for (int c = 0; c < 3; ++c) A.re[c] = A.im[c] = make_float2(0.f, 0.f);
 #pragma unroll
         for (int mu = 0; mu < 4; ++mu) {
             int jfA, jbA, jfB, jbB;
@@ -284,23 +143,28 @@ __global__ void __launch_bounds__(kBlock, STG_FX2_MINBLOCKS) k_dslash_fx2(const 
             load_field2(a.in, jbA, jbB, v);
             bwd2<R>(u, v, s2b, A);
         }
-        const f2 k = make_float2(LinkPost<PX16>::k, LinkPost<PX16>::k);
-        Vec3<float> accA, accB;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const f2 re = mul2(sub2(A.pr[c], A.nr[c]), k);
-            const f2 im = mul2(sub2(A.pi[c], A.ni[c]), k);
-            accA.r[c] = re.x;
-            accA.i[c] = im.x;
-            accB.r[c] = re.y;
-            accB.i[c] = im.y;
-        }
         const float m2 = (EPI == EPI_A_CG) ? float(a.state->m2) : float(a.m2);
-        const float dA = epilogue<EPI>(a, vh, iA, accA, m2, wA);
-        float dB = 0.f;
-        if (okB) dB = epilogue<EPI>(a, vh, iB, accB, m2, wB);
-        dot.hi = dA;
-        dot = ff_add(dot, FF{dB, 0.f});
+        f2 dA_B;
+        if (EPI == EPI_RES) {
+            const f2 k = make_float2(LinkPost<PX16>::k, LinkPost<PX16>::k);
+            Vec3<float> accA, accB;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const f2 re = mul2(A.re[c], k);
+                const f2 im = mul2(A.im[c], k);
+                accA.r[c] = re.x;
+                accA.i[c] = im.x;
+                accB.r[c] = re.y;
+                accB.i[c] = im.y;
+            }
+            dA_B.x = epilogue<EPI>(a, vh, iA, accA, m2, wA);
+            dA_B.y = okB ? epilogue<EPI>(a, vh, iB, accB, m2, wB) : 0.f;
+        } else {
+            dA_B = finish_pair<EPI>(a, iA, iB, true, okB, A, m2, wA, wB);
+            if (!okB) dA_B.y = 0.f;  // a missing B recomputed site A
+        }
+        dot.hi = dA_B.x;
+        dot = ff_add(dot, FF{dA_B.y, 0.f});
     }
     if (EPI == EPI_A_DOT || EPI == EPI_A_CG || EPI == EPI_RES) {
         double total;
@@ -437,7 +301,7 @@ __global__ void __launch_bounds__(kFxCons, kFxCtasPerSM) k_dslash_fx2_staged(con
         const Site sB = site_of(a.g, jB, a.parity);
         Acc2 A;
 #pragma unroll
-        for (int k = 0; k < 3; ++k) A.pr[k] = A.nr[k] = A.pi[k] = A.ni[k] = make_float2(0.f, 0.f);
+        for (int k = 0; k < 3; ++k) A.re[k] = A.im[k] = make_float2(0.f, 0.f);
         bool alive = true;
 #pragma unroll
         for (int mu = 0; mu < 4; ++mu) {
@@ -497,23 +361,29 @@ __global__ void __launch_bounds__(kFxCons, kFxCtasPerSM) k_dslash_fx2_staged(con
             dot.hi = __int_as_float(0x7fc00000);  // the grid sum becomes NaN
             break;
         }
-        const f2 kk = make_float2(LinkPost<PX16>::k, LinkPost<PX16>::k);
-        Vec3<float> accA, accB;
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-            const f2 re = mul2(sub2(A.pr[q], A.nr[q]), kk);
-            const f2 im = mul2(sub2(A.pi[q], A.ni[q]), kk);
-            accA.r[q] = re.x;
-            accA.i[q] = im.x;
-            accB.r[q] = re.y;
-            accB.i[q] = im.y;
-        }
         const float m2 = (EPI == EPI_A_CG) ? float(a.state->m2) : float(a.m2);
-        float dA = 0.f, dB = 0.f;
-        if (okA) dA = epilogue<EPI>(a, vh, iA, accA, m2, wA);
-        if (okB) dB = epilogue<EPI>(a, vh, iB, accB, m2, wB);
-        dot = ff_add(dot, FF{dA, 0.f});
-        dot = ff_add(dot, FF{dB, 0.f});
+        f2 dA_B;
+        if (EPI == EPI_RES) {
+            const f2 kk = make_float2(LinkPost<PX16>::k, LinkPost<PX16>::k);
+            Vec3<float> accA, accB;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const f2 re = mul2(A.re[q], kk);
+                const f2 im = mul2(A.im[q], kk);
+                accA.r[q] = re.x;
+                accA.i[q] = im.x;
+                accB.r[q] = re.y;
+                accB.i[q] = im.y;
+            }
+            dA_B.x = okA ? epilogue<EPI>(a, vh, iA, accA, m2, wA) : 0.f;
+            dA_B.y = okB ? epilogue<EPI>(a, vh, iB, accB, m2, wB) : 0.f;
+        } else {
+            dA_B = finish_pair<EPI>(a, iA, iB, okA, okB, A, m2, wA, wB);
+            if (!okA) dA_B.x = 0.f;
+            if (!okB) dA_B.y = 0.f;
+        }
+        dot = ff_add(dot, FF{dA_B.x, 0.f});
+        dot = ff_add(dot, FF{dA_B.y, 0.f});
     }
     __syncthreads();
     if (c == 0 && abort_flag) {

@@ -30,7 +30,7 @@ __device__ __forceinline__ Vec3<typename Real<P>::T> dslash_site(const Geom &g, 
         const T s2b = (R == 12) ? T(sb * LinkPost<P>::row2) : T(1);
         const Mat3<T> uf = LinkIO<P, R>::load(lf[mu], vh, i);
         const Vec3<T> vf = FieldIO<P>::load_nc(in, vh, jf);
-        mul_add(uf, vf, acc, s2f);
+        mul_add<R == 12>(uf, vf, acc, s2f);
         const Mat3<T> ub = LinkIO<P, R>::load(lb[mu], vh, jb);
         const Vec3<T> vb = FieldIO<P>::load_nc(in, vh, jb);
         adj_mul_sub(ub, vb, acc, s2b);

@@ -50,12 +50,23 @@ static bool same_key(const TuneEntry &e, const int *dims, int prec, int recon, i
 }
 
 // shapes 0 .. kMrhsShapes - 1: register-fed (NB, TPS); then the staged
-// kernel with NB = ms_nb(shape - kMrhsShapes) (12-real FP32 / FX16 links)
-static bool valid_choice(int shape) { return shape >= 0 && shape < kMrhsShapes + kMrhsStagedShapes; }
+// kernel with NB = ms_nb(shape - kMrhsShapes) (12-real FP32 / FX16 links);
+// then (FX16 / 12-real only) the staged kernel with two sites per thread,
+// NB = msp_nb(shape - kMrhsShapes - kMrhsStagedShapes)
+constexpr int kMspFirst = kMrhsShapes + kMrhsStagedShapes;
+constexpr int kMspCount = 2;  // NB = 2, 4 (mrhs_paired.cuh)
+static bool valid_choice(int shape) { return shape >= 0 && shape < kMspFirst + kMspCount; }
 
 static bool staged_ok(const LinkField *lf)
 {
     return lf->mtiled && lf->recon == 12 && (lf->prec == P32 || lf->prec == PX16);
+}
+
+static bool shape_ok(const LinkField *lf, int shape)
+{
+    if (shape < kMrhsShapes) return true;
+    if (shape < kMspFirst) return staged_ok(lf);
+    return staged_ok(lf) && lf->prec == PX16;
 }
 
 static void tune_load_file_locked()
@@ -124,9 +135,14 @@ static stg_status launch_m(const stg_gauge *g, const LinkField *lf, int shape, i
         a.lb[mu] = lf->blk(1 - a.parity, mu);
     }
     a.lt = nullptr;
+    // STG_MRHS_GRID caps the staged kernels' CTA count (more tiles per CTA;
+    // for tests)
+    a.grid_limit = 0;
+    if (const char *v = getenv("STG_MRHS_GRID")) a.grid_limit = atoi(v) > 0 ? atoi(v) : 0;
     if (shape >= kMrhsShapes) {
-        if (!staged_ok(lf)) {
-            set_error("multi-system Dslash: the staged kernel needs the tile-major 12-real links");
+        if (!shape_ok(lf, shape)) {
+            set_error("multi-system Dslash: the staged kernel needs the tile-major 12-real links "
+                      "(FP32 or FX16; two sites per thread: FX16)");
             return STG_ERR_UNSUPPORTED;
         }
         a.lt = lf->mtiled + (size_t)a.parity * lf->mtiled_parity_bytes;
@@ -149,7 +165,7 @@ static bool forced_shape(const LinkField *lf, int n, int *shape)
     const char *v = getenv("STG_MRHS_SHAPE");
     if (!v) return false;
     const int k = atoi(v);
-    if (!valid_choice(k) || !(k < kMrhsShapes ? mrhs_tps(k) <= n : staged_ok(lf))) return false;
+    if (!valid_choice(k) || !(k < kMrhsShapes ? mrhs_tps(k) <= n : shape_ok(lf, k))) return false;
     *shape = k;
     return true;
 }
@@ -162,8 +178,7 @@ static stg_status tune(const stg_gauge *g, const LinkField *lf, int n, const voi
                        size_t fstride, cudaStream_t s, int *shape_out)
 {
     if (forced_shape(lf, n, shape_out)) return STG_OK;
-    if (tune_lookup(g->dims, lf->prec, lf->recon, n, shape_out) &&
-        (*shape_out < kMrhsShapes || staged_ok(lf)))
+    if (tune_lookup(g->dims, lf->prec, lf->recon, n, shape_out) && shape_ok(lf, *shape_out))
         return STG_OK;
     cudaEvent_t e0, e1;
     STG_CUDA(cudaEventCreate(&e0));
@@ -175,14 +190,18 @@ static stg_status tune(const stg_gauge *g, const LinkField *lf, int n, const voi
     float best = 1e30f;
     int bshape = 0;
     stg_status st = STG_OK;
-    for (int k = 0; k < kMrhsShapes + kMrhsStagedShapes && st == STG_OK; ++k) {
+    for (int k = 0; k < kMspFirst + kMspCount && st == STG_OK; ++k) {
         if (k < kMrhsShapes) {
             if (mrhs_tps(k) > n || (mrhs_tps(k) == 1 && mrhs_nb(k) > n && mrhs_nb(k) > 1)) continue;
-        } else {
+        } else if (k < kMspFirst) {
             // the site groups of a staged CTA share the systems: a block
             // larger than a group's share only adds idle slots
             const int nb = ms_nb(k - kMrhsShapes);
             if (!staged_ok(lf) || (nb > 2 && nb > (n + kMsGroups - 1) / kMsGroups)) continue;
+        } else {
+            // four warps share the systems (two sites per thread)
+            const int nb = k == kMspFirst ? 2 : 4;
+            if (!shape_ok(lf, k) || (nb > 2 && nb > (n + 3) / 4)) continue;
         }
         MrhsArgs a = {};
         a.parity = 1;
@@ -898,7 +917,10 @@ stg_status stg_mrhs_tuning(const stg_gauge *g, stg_prec prec, int nrhs, int *rhs
         set_error("stg_mrhs_tuning: not tuned yet for this lattice, precision and nrhs");
         return STG_ERR_INVALID_ARG;
     }
-    if (shape >= kMrhsShapes) {
+    if (shape >= kMspFirst) {
+        *rhs_block = shape == kMspFirst ? 2 : 4;
+        *threads_per_site = -1;  // staged, two sites per thread (FX16 / 12-real)
+    } else if (shape >= kMrhsShapes) {
         *rhs_block = ms_nb(shape - kMrhsShapes);
         *threads_per_site = 0;  // staged: one link load per site serves all systems
     } else {

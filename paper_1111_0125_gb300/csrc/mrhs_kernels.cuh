@@ -42,6 +42,8 @@ struct MrhsArgs {
     float2 *partials;      // EPI_A_CG: [nrhs][gridDim.x]
     unsigned *counter;     // EPI_A_CG: arrival counter
     int grid_cap;          // blocks launched at most (they stride over site tiles)
+    int grid_limit;        // staged kernels: at most this many CTAs (0 = all resident;
+                           // STG_MRHS_GRID, read per call, for tests)
     const char *lt;        // staged kernel: tile-major links of the output parity
 };
 
@@ -122,7 +124,7 @@ __global__ void __launch_bounds__(kMrhsBlock) k_dslash_m(const MrhsArgs a)
 #pragma unroll
                 for (int q = 0; q < NB; ++q) v[q] = FieldIO<P>::load_nc(a.in + rid[q] * a.fstride, vh, jf[mu]);
 #pragma unroll
-                for (int q = 0; q < NB; ++q) mul_add(uf, v[q], acc[q], s2f[mu]);
+                for (int q = 0; q < NB; ++q) mul_add<R == 12>(uf, v[q], acc[q], s2f[mu]);
                 const Mat3<T> ub = LinkIO<P, R>::load(a.lb[mu], vh, jb[mu]);
 #pragma unroll
                 for (int q = 0; q < NB; ++q) v[q] = FieldIO<P>::load_nc(a.in + rid[q] * a.fstride, vh, jb[mu]);
@@ -639,11 +641,7 @@ void launch_ms_nb(int epi, const MrhsArgs &a, cudaStream_t s)
     }();
     const int ntiles = (a.g.Vh + kMTile - 1) / kMTile;
     int cap = resident;
-    // STG_MRHS_GRID caps the CTA count (more tiles per CTA; for tests)
-    if (const char *v = getenv("STG_MRHS_GRID")) {
-        const int c = atoi(v);
-        if (c > 0 && c < cap) cap = c;
-    }
+    if (a.grid_limit > 0 && a.grid_limit < cap) cap = a.grid_limit;
     const int grid = ntiles < cap ? ntiles : cap;
     switch (epi) {
     case EPI_NONE: k_dslash_ms<P, NB, EPI_NONE><<<grid, kMsThreads, smem, s>>>(a); break;

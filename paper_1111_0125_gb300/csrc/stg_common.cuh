@@ -302,20 +302,40 @@ __device__ __forceinline__ float fx_hi(unsigned w)
 {
     return __int_as_float((int)__byte_perm(w, 0x4B40u, 0x5432)) - 12615680.0f;
 }
-// Encoding: x (already scaled to [-32767, 32767]) plus 1.5 * 2^23 + 32768
-// rounds to the nearest integer in FP32, leaving rint(x) + 32768 in the low
-// 16 bits; one byte permute packs the (re, im) pair.
+// Encoding: x (already scaled by 1 / s) plus 1.5 * 2^23 + 32768 rounds to
+// the nearest integer in FP32, leaving rint(x) + 32768 in the low 16 bits;
+// one byte permute packs the (re, im) pair.  No clamp is needed: with s from
+// fx_scale and k = RN(1 / s), |x| <= 32767 (1 + 2^-21) < 32767.5 for every
+// finite component, so rint(x) + 32768 stays in [1, 65535].
 __device__ __forceinline__ unsigned fx_pack(float re, float im)
 {
-    re = fminf(fmaxf(re, -32767.f), 32767.f);
-    im = fminf(fmaxf(im, -32767.f), 32767.f);
     const unsigned a = __float_as_uint(re + 12615680.0f);
     const unsigned b = __float_as_uint(im + 12615680.0f);
     return __byte_perm(a, b, 0x5410);
 }
 
+// maximum that returns NaN when either operand is NaN (max.NaN, sm_80+): a
+// NaN component makes the site's scale NaN, so it decodes as NaN instead of
+// turning into a finite fixed-point value
+__device__ __forceinline__ float fmax_nan(float a, float b)
+{
+    float d;
+    asm("max.NaN.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
+    return d;
+}
+
 // PX16 field: one 16-byte record {3 words of (re, im) fixed point, f32 s}
-// with value = q * s and s = max |component| / 32767 of the site.
+// with value = q * s and s = max |component| / 32767 of the site, rounded up
+// to 15 significant bits.  With s that short, K s is exact in FP32 for the
+// decode's 9-bit offset K = 1.5 * 2^23 + 32768, so a decoder may form q s
+// from the biased value (K + q) as one FMA, (K + q) s - K s, with the same
+// single rounding as q s (the packed Dslash kernels do).
+__device__ __forceinline__ float fx_scale(float m)
+{
+    const float s = m * (1.0f / 32767.0f);
+    return __uint_as_float((__float_as_uint(s) + 0x1FFu) & ~0x1FFu);
+}
+
 template <> struct FieldIO<PX16> {
     template <bool NC = false>
     __device__ __forceinline__ static Vec3<float> load(const void *f, int vh, int s)
@@ -336,9 +356,9 @@ template <> struct FieldIO<PX16> {
     {
         float m = 0.f;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) m = fmaxf(m, fmaxf(fabsf(v.r[c]), fabsf(v.i[c])));
-        const float k = m > 0.f ? 32767.0f / m : 0.f;
-        const float sc = m * (1.0f / 32767.0f);
+        for (int c = 0; c < 3; ++c) m = fmax_nan(m, fmax_nan(fabsf(v.r[c]), fabsf(v.i[c])));
+        const float sc = fx_scale(m);
+        const float k = m > 0.f ? 1.0f / sc : 0.f;
         uint4 u;
         u.x = fx_pack(v.r[0] * k, v.i[0] * k);
         u.y = fx_pack(v.r[1] * k, v.i[1] * k);
@@ -552,25 +572,44 @@ template <> struct LinkPost<PX16> {
     static constexpr float row2 = 1.0f / 32767.0f;
 };
 
-// acc += U v, with row 2 of U scaled by s2 (the 12-real sign; 1 for 18-real)
-template <typename T>
+// a * b + c with one rounding, in the precision of T
+__device__ __forceinline__ float fmat(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fmat(double a, double b, double c) { return fma(a, b, c); }
+
+// acc += U v, with row 2 of U scaled by s2 (the 12-real sign; 1 for 18-real).
+// Every product goes into its accumulator by one FMA (two per real part of
+// a complex product): written as acc += (a b - c d), the compiler would need
+// a multiply, an FMA and an add, which costs the ALU-bound FP64 operator a
+// third more FP64 instructions.
+// SCALED_ROW2: row 2 carries the factor s2 (12-real links); otherwise s2
+// must be 1 and row 2 accumulates like rows 0 and 1.
+template <bool SCALED_ROW2 = true, typename T>
 __device__ __forceinline__ void mul_add(const Mat3<T> &u, const Vec3<T> &v, Vec3<T> &acc, T s2)
 {
+    constexpr int nrow = SCALED_ROW2 ? 2 : 3;
 #pragma unroll
-    for (int a = 0; a < 2; ++a)
+    for (int a = 0; a < nrow; ++a)
 #pragma unroll
         for (int b = 0; b < 3; ++b) {
-            acc.r[a] += u.r[a][b] * v.r[b] - u.i[a][b] * v.i[b];
-            acc.i[a] += u.r[a][b] * v.i[b] + u.i[a][b] * v.r[b];
+            acc.r[a] = fmat(u.r[a][b], v.r[b], acc.r[a]);
+            acc.r[a] = fmat(-u.i[a][b], v.i[b], acc.r[a]);
+            acc.i[a] = fmat(u.r[a][b], v.i[b], acc.i[a]);
+            acc.i[a] = fmat(u.i[a][b], v.r[b], acc.i[a]);
         }
-    T wr = T(0), wi = T(0);
+    if (SCALED_ROW2) {
+        T wr = u.r[2][0] * v.r[0], wi = u.r[2][0] * v.i[0];
+        wr = fmat(-u.i[2][0], v.i[0], wr);
+        wi = fmat(u.i[2][0], v.r[0], wi);
 #pragma unroll
-    for (int b = 0; b < 3; ++b) {
-        wr += u.r[2][b] * v.r[b] - u.i[2][b] * v.i[b];
-        wi += u.r[2][b] * v.i[b] + u.i[2][b] * v.r[b];
+        for (int b = 1; b < 3; ++b) {
+            wr = fmat(u.r[2][b], v.r[b], wr);
+            wr = fmat(-u.i[2][b], v.i[b], wr);
+            wi = fmat(u.r[2][b], v.i[b], wi);
+            wi = fmat(u.i[2][b], v.r[b], wi);
+        }
+        acc.r[2] = fmat(s2, wr, acc.r[2]);
+        acc.i[2] = fmat(s2, wi, acc.i[2]);
     }
-    acc.r[2] += s2 * wr;
-    acc.i[2] += s2 * wi;
 }
 
 // acc -= U^dag v, (U^dag)_{ab} = conj(U_{ba}), row 2 of U scaled by s2
@@ -582,11 +621,16 @@ __device__ __forceinline__ void adj_mul_sub(const Mat3<T> &u, const Vec3<T> &v, 
     for (int a = 0; a < 3; ++a) {
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
-            acc.r[a] -= u.r[b][a] * v.r[b] + u.i[b][a] * v.i[b];
-            acc.i[a] -= u.r[b][a] * v.i[b] - u.i[b][a] * v.r[b];
+            // conj(U_ba) v_b = (u.r v.r + u.i v.i) + i (u.r v.i - u.i v.r)
+            acc.r[a] = fmat(-u.r[b][a], v.r[b], acc.r[a]);
+            acc.r[a] = fmat(-u.i[b][a], v.i[b], acc.r[a]);
+            acc.i[a] = fmat(-u.r[b][a], v.i[b], acc.i[a]);
+            acc.i[a] = fmat(u.i[b][a], v.r[b], acc.i[a]);
         }
-        acc.r[a] -= u.r[2][a] * v2r + u.i[2][a] * v2i;
-        acc.i[a] -= u.r[2][a] * v2i - u.i[2][a] * v2r;
+        acc.r[a] = fmat(-u.r[2][a], v2r, acc.r[a]);
+        acc.r[a] = fmat(-u.i[2][a], v2i, acc.r[a]);
+        acc.i[a] = fmat(-u.r[2][a], v2i, acc.i[a]);
+        acc.i[a] = fmat(u.i[2][a], v2r, acc.i[a]);
     }
 }
 

@@ -23,6 +23,13 @@ usage measured during the run (live torch allocations of the engine plus the
 library's bytes of every live handle and session).  Latency is measured per
 request from its arrival to the moment its solution is back in host memory.
 
+With `group_max_vh` > 0, requests on lattices of at most that many sites per
+parity go to lattice-group sessions (``stg_lgroup_*``) instead: systems of
+different small lattices and gauge fields share one session and iterate in
+lock-step, four launches per iteration for all of them, on one stream and
+one host thread.  A gauge field stays resident while any of its requests is
+in a group.
+
 With `priority_by_size`, sessions of smaller lattices run on higher-priority
 CUDA streams, so their short kernels are scheduled ahead of the long
 kernels of large lattices (shortest job first at the level of thread
@@ -42,7 +49,9 @@ import numpy as np
 import torch
 
 from . import (STG_FP32, STG_OK, stg_batch_add, stg_batch_bytes, stg_batch_create,
-               stg_batch_destroy, stg_batch_step, stg_cg_params_default, stg_gauge_bytes)
+               stg_batch_destroy, stg_batch_step, stg_cg_params_default, stg_gauge_bytes,
+               stg_lgroup_add, stg_lgroup_bytes, stg_lgroup_create, stg_lgroup_destroy,
+               stg_lgroup_step)
 from .fields import Gauge
 
 
@@ -165,6 +174,87 @@ class _Session:
                 eng._wake()
 
 
+def group_bytes(slots: int, max_vh: int, sloppy: int) -> int:
+    """Device bytes of one lattice-group session: the library's count plus a
+    complex128 source and solution buffer of max_vh sites for every slot."""
+    return stg_lgroup_bytes(slots, max_vh, sloppy) + 2 * slots * max_vh * 48
+
+
+class _GroupSession(_Session):
+    """A lattice-group session: its slots take requests on any resident
+    gauge field of at most max_vh sites per parity."""
+
+    def __init__(self, engine, device, priority=0):
+        self.engine = engine
+        self.entry = None
+        self.stream = torch.cuda.Stream(device=device, priority=priority)
+        params = stg_cg_params_default(None)
+        params.sloppy = engine.sloppy
+        params.delta = engine.group_delta
+        params.check_every = engine.chunk
+        self.max_vh = engine.group_max_vh
+        self.nslots = engine.group_slots
+        self.handle = stg_lgroup_create(self.nslots, self.max_vh, engine.sloppy, engine.recon,
+                                        params, self.stream)
+        self.lib_bytes = stg_lgroup_bytes(self.nslots, self.max_vh, engine.sloppy)
+        self.bytes = group_bytes(self.nslots, self.max_vh, engine.sloppy)
+        self.device = device
+        self.busy = {}
+        self.inbox = collections.deque()
+        self.cv = threading.Condition()
+        self.stop = False
+        self.thread = threading.Thread(target=self._run, daemon=True)
+        self.thread.start()
+
+    def free_slots(self) -> int:
+        return self.nslots - self.load()
+
+    def close(self):
+        with self.cv:
+            self.stop = True
+            self.cv.notify()
+        self.thread.join()
+        stg_lgroup_destroy(self.handle)
+
+    def _admit(self, item):
+        req, entry = item
+        host = self.engine.sources[req.source_key]
+        vh = entry.gauge.vh
+        with torch.cuda.stream(self.stream):
+            src = torch.empty((vh, 3), dtype=torch.complex128, device=self.device)
+            src.copy_(host, non_blocking=True)
+            x = torch.zeros_like(src)
+        self.engine._sample_memory()
+        slot = stg_lgroup_add(self.handle, entry.gauge.handle, src, x, req.mass, req.tol)
+        self.busy[slot] = (item, src, x)
+
+    def _run(self):
+        torch.cuda.set_device(self.engine.device)
+        eng = self.engine
+        while True:
+            with self.cv:
+                while not self.stop and not self.inbox and not self.busy:
+                    self.cv.wait()
+                if self.stop and not self.busy and not self.inbox:
+                    return
+                new = []
+                while self.inbox and len(self.busy) + len(new) < self.nslots:
+                    new.append(self.inbox.popleft())
+            for item in new:
+                self._admit(item)
+            done, _ = stg_lgroup_step(self.handle, self.nslots)
+            for slot, status, st in done:
+                (req, entry), src, x = self.busy.pop(slot)
+                with torch.cuda.stream(self.stream):
+                    xh = x.to("cpu", non_blocking=True)
+                self.stream.synchronize()
+                with eng.lock:
+                    entry.in_groups -= 1
+                eng._complete(req, status, st, xh.numpy() if eng.keep_solutions else None)
+            if done:
+                eng._wake()
+
+
 @dataclasses.dataclass
 class _GaugeEntry:
     key: object
@@ -172,6 +262,7 @@ class _GaugeEntry:
     bytes: int
     sessions: list
     last_used: float
+    in_groups: int = 0      # requests of this field inside lattice-group sessions
 
 
 class ServeEngine:
@@ -184,7 +275,8 @@ class ServeEngine:
     def __init__(self, gauges: dict, sources: dict, hbm_budget: float = 120e9, slots: int = 4,
                  max_sessions_per_gauge: int = 2, max_resident: int = 8, sloppy: int = STG_FP32,
                  recon: int = 12, chunk: int = 16, keep_solutions: bool = False, device: int = 0,
-                 priority_by_size: bool = True):
+                 priority_by_size: bool = True, group_max_vh: int = 0, group_slots: int = 8,
+                 max_groups: int = 2, group_delta: float | None = None):
         self.gauge_src = gauges
         self.sources = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory()
                         for k, v in sources.items()}
@@ -198,6 +290,13 @@ class ServeEngine:
         self.keep_solutions = keep_solutions
         self.device = device
         self.priority_by_size = priority_by_size
+        self.group_max_vh = int(group_max_vh)
+        self.group_slots = int(group_slots)
+        self.max_groups = int(max_groups)
+        # the library's per-precision default reliable-update threshold
+        self.group_delta = (group_delta if group_delta is not None else
+                            0.1 if sloppy == 0 else 0.05 if sloppy == STG_FP32 else 0.25)
+        self.groups: list = []
         vols = sorted({int(np.prod(d)) for d, _ in gauges.values()})
         # stream priority per lattice volume: 0 for the largest, one step
         # higher (more negative) per distinct larger volume
@@ -229,6 +328,7 @@ class ServeEngine:
         for e in list(self.resident.values()):
             n += e.bytes
             n += sum(s.lib_bytes for s in list(e.sessions))
+        n += sum(s.lib_bytes for s in list(self.groups))
         return n
 
     def _sample_memory(self):
@@ -242,6 +342,35 @@ class ServeEngine:
             self.peak_used = float(self.used)
 
     # -- placement ----------------------------------------------------------
+    def _idle_gauges(self, keep=None):
+        return [g for g in self.resident.values()
+                if g is not keep and all(s.load() == 0 for s in g.sessions) and g.in_groups == 0]
+
+    def _make_room(self, need, keep=None, slots_for_gauge=False) -> bool:
+        """Evict idle gauge fields (least recently used first, never `keep`)
+        and close idle lattice-group sessions until `need` more bytes fit the
+        budget (and, for a new field, the resident count allows one more).
+        False if nothing idle is left to free."""
+        while (self.used + need > self.budget or
+               (slots_for_gauge and len(self.resident) >= self.max_resident)):
+            idle = self._idle_gauges(keep)
+            if idle:
+                self._evict(min(idle, key=lambda g: g.last_used))
+                continue
+            idle_groups = [g for g in self.groups if g.load() == 0]
+            if idle_groups and self.used + need > self.budget:
+                g = idle_groups[0]
+                g.close()
+                self.used -= g.bytes
+                self.groups.remove(g)
+                continue
+            return False
+        return True
+
+    def _busy(self) -> int:
+        n = sum(s.load() for e in self.resident.values() for s in e.sessions)
+        return n + sum(g.load() for g in self.groups)
+
     def _gauge(self, key):
         e = self.resident.get(key)
         if e is not None:
@@ -249,12 +378,8 @@ class ServeEngine:
         dims, links = self.gauge_src[key]
         need = gauge_bytes(dims, self.sloppy, self.recon)
         # evict idle gauges while over the resident count or the budget
-        while (len(self.resident) >= self.max_resident or self.used + need > self.budget):
-            idle = [g for g in self.resident.values() if all(s.load() == 0 for s in g.sessions)]
-            if not idle:
-                return None
-            victim = min(idle, key=lambda g: g.last_used)
-            self._evict(victim)
+        if not self._make_room(need, slots_for_gauge=True):
+            return None
         g = Gauge(dims, links, sloppy=self.sloppy, recon=self.recon, stream=self.upload_stream)
         e = _GaugeEntry(key, g, need, [], time.perf_counter())
         self.resident[key] = e
@@ -270,18 +395,38 @@ class ServeEngine:
         self.used -= e.bytes
         del self.resident[e.key]
 
+    def _place_group(self, req, e) -> bool:
+        open_g = [s for s in self.groups if s.free_slots() > 0]
+        if not open_g and len(self.groups) < self.max_groups:
+            need = group_bytes(self.group_slots, self.group_max_vh, self.sloppy)
+            if self.used + need <= self.budget or self._make_room(need, keep=e):
+                prio = min(self._prio.values()) if self.priority_by_size else 0
+                g = _GroupSession(self, self.device, prio)
+                self.used += g.bytes
+                self.groups.append(g)
+                self._sample_memory()
+                open_g = [g]
+        if not open_g:
+            return False
+        with self.lock:
+            e.in_groups += 1
+        min(open_g, key=lambda s: s.load()).submit((req, e))
+        return True
+
     def _place(self, req) -> bool:
         e = self._gauge(req.gauge_key)
         if e is None:
             return False
         e.last_used = time.perf_counter()
+        if self.group_max_vh > 0 and e.gauge.vh <= self.group_max_vh:
+            return self._place_group(req, e)
         open_s = [s for s in e.sessions if s.free_slots() > 0]
         if open_s:
             min(open_s, key=lambda s: s.load()).submit(req)
             return True
         if len(e.sessions) < self.max_sessions:
             need = session_bytes(e.gauge, self.slots, self.sloppy)
-            if self.used + need <= self.budget:
+            if self.used + need <= self.budget or self._make_room(need, keep=e):
                 prio = 0
                 if self.priority_by_size:
                     prio = self._prio.get(int(np.prod(self.gauge_src[e.key][0])), 0)
@@ -303,6 +448,7 @@ class ServeEngine:
         todo = collections.deque(sorted(requests, key=lambda r: r.arrival))
         self.t0 = time.perf_counter()
         n = len(todo)
+        stall_since, last_finished = None, -1
         while True:
             now = time.perf_counter() - self.t0
             while todo and (not realtime or todo[0].arrival <= now):
@@ -321,6 +467,18 @@ class ServeEngine:
                 finished = len(self.results)
             if finished == n:
                 break
+            if pending and self._busy() == 0 and finished == last_finished:
+                # nothing runs and nothing idle is left to evict: for a few
+                # seconds no request could be placed (its field and session
+                # alone exceed the budget)
+                if stall_since is None:
+                    stall_since = time.perf_counter()
+                elif time.perf_counter() - stall_since > 5.0:
+                    raise RuntimeError(f"request {pending[0].rid} cannot be admitted within the "
+                                       f"HBM budget of {self.budget:.0f} bytes")
+            else:
+                stall_since = None
+            last_finished = finished
             wait = 0.05
             if todo and realtime:
                 wait = min(wait, max(0.0, todo[0].arrival - (time.perf_counter() - self.t0)))
@@ -329,6 +487,10 @@ class ServeEngine:
         return sorted(self.results, key=lambda r: r.rid)
 
     def close(self):
+        for g in self.groups:
+            g.close()
+            self.used -= g.bytes
+        self.groups = []
         for e in list(self.resident.values()):
             self._evict(e)
 

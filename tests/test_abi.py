@@ -129,3 +129,16 @@ def test_group_launch_argument_checks(stg):
     assert e.value.status == stg.STG_ERR_INVALID_ARG
     with pytest.raises(ValueError):
         stg.stg_dslash_group([0, 0], [0], [0], [0], stg.STG_FP32, stream=0)
+
+
+def test_lattice_group_host_checks(stg):
+    # rejected before any CUDA call
+    assert stg.stg_lgroup_bytes(0, 128, stg.STG_FP32) == 0
+    assert stg.stg_lgroup_bytes(17, 128, stg.STG_FP32) == 0
+    for n, vh, recon in [(0, 128, 12), (17, 128, 12), (4, 0, 12), (4, 128, 10)]:
+        with pytest.raises(stg.StgError) as e:
+            stg.stg_lgroup_create(n, vh, stg.STG_FP32, recon, stream=0)
+        assert e.value.status == stg.STG_ERR_INVALID_ARG
+    with pytest.raises(stg.StgError) as e:
+        stg.stg_lgroup_create(4, 128, 9, 12, stream=0)
+    assert e.value.status == stg.STG_ERR_INVALID_ARG

@@ -121,6 +121,49 @@ def test_staged_mrhs_matches_register_fed(monkeypatch, prec, shape, nb, grid):
             assert np.linalg.norm(r) <= 1e-10 * np.linalg.norm(chis[k]), k
 
 
+@pytest.mark.parametrize("shape,nb", [("12", 2), ("13", 4)])
+@pytest.mark.parametrize("grid", [None, "2"])
+@pytest.mark.parametrize("n", [9, 16])
+def test_paired_staged_mrhs(monkeypatch, shape, nb, grid, n):
+    """The FX16 staged multi-system kernel with two sites per thread (site
+    pairs in the halves of FP32x2 registers) against the register-fed
+    kernel and the oracle: Dslash of both parities, A, and a batched CG; a
+    grid of 2 CTAs walks 12 of the 23 tiles each (ragged last tile)."""
+    prec = stg.STG_FX16
+    dims = (6, 4, 10, 12)
+    U = gen.gauge_field(dims, "exp", seed=6, eps=0.5)
+    chis = list(gen.source(dims, seed=8, nrhs=n))
+    masses = gen.log_uniform(n, 0.005, 0.05, seed=10)
+    with stg.Gauge(dims, U, sloppy=prec, recon=12) as g:
+        buf, fb = _pack_batch(g, chis, prec)
+        ins = _unpack_batch(g, buf, fb, n, prec)
+        monkeypatch.setenv("STG_MRHS_SHAPE", "2")  # register-fed, NB = 4
+        ref = torch.empty_like(buf)
+        stg.stg_dslash_mrhs(g.handle, 1, n, buf, ref, prec)
+        ref = _unpack_batch(g, ref, fb, n, prec)
+        monkeypatch.setenv("STG_MRHS_SHAPE", shape)
+        assert stg.stg_mrhs_tuning(g.handle, prec, n) == (nb, -1)
+        if grid is not None:
+            monkeypatch.setenv("STG_MRHS_GRID", grid)
+        for parity in (0, 1):
+            out = torch.empty_like(buf)
+            stg.stg_dslash_mrhs(g.handle, parity, n, buf, out, prec)
+            got = _unpack_batch(g, out, fb, n, prec)
+            for k in range(n):
+                assert rel(got[k], oracle.dslash(dims, U, ins[k], parity)) < TOL[prec], (k, parity)
+                if parity == 1:
+                    assert rel(got[k], ref[k]) < TOL[prec], k
+        out = torch.empty_like(buf)
+        stg.stg_apply_A_mrhs(g.handle, n, masses, buf, out, prec)
+        got = _unpack_batch(g, out, fb, n, prec)
+        for k in range(n):
+            assert rel(got[k], oracle.apply_A(dims, U, masses[k], ins[k])) < TOL[prec], k
+        xs, st = _solve_batch(g, chis, masses, 1e-10, prec)
+        for k in range(n):
+            r = chis[k] - oracle.apply_A(dims, U, masses[k], xs[k])
+            assert np.linalg.norm(r) <= 1e-10 * np.linalg.norm(chis[k]), k
+
+
 def _solve_batch(g, bs, masses, tol, sloppy, policy=stg.STG_CG_RELIABLE):
     n = len(bs)
     src = torch.from_numpy(np.ascontiguousarray(np.stack(bs))).cuda()

@@ -175,3 +175,21 @@ def test_batch_session_join_while_running():
         for k in range(3):
             r = bs[k] - oracle.apply_A(dims, U, masses[k], xs[k].cpu().numpy())
             assert np.linalg.norm(r) <= tol * np.linalg.norm(bs[k])
+
+
+def test_small_lattices_served_through_lattice_groups():
+    """Requests on the two small lattices go to lattice-group sessions
+    (systems of different lattices and gauge fields in lock-step), the rest
+    to per-field batch sessions; every result is the one the request gets
+    alone, within the budget."""
+    gauges, sources = _tables()
+    reqs = _requests(24, seed=9)
+    eng = ServeEngine(gauges, sources, slots=2, max_sessions_per_gauge=1, keep_solutions=True,
+                      group_max_vh=int(np.prod((6, 4, 10, 12))) // 2, group_slots=4, max_groups=2)
+    try:
+        results = eng.run(reqs, realtime=False)
+        assert len(eng.groups) >= 1
+        assert eng.peak_measured <= eng.budget
+    finally:
+        eng.close()
+    _check(results, reqs, gauges, sources)
