@@ -45,6 +45,7 @@ LINK_BYTES = {("f64", 18): 144, ("f64", 12): 96, ("f32", 18): 72, ("f32", 12): 4
               ("bf16", 18): 36, ("bf16", 12): 24}
 FIELD_BYTES = {"f64": 48, "f32": 24, "f16": 16, "fx16": 16, "bf16": 16}
 FALLBACK_HBM_GBS = 6800.0
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # 80.5: SMs x FP32 lanes x flop per FMA x clock
 def workload_name(dims, tol):
     lx, ly, lz, lt = dims
     lat = f"{lx}^3x{lt}" if lx == ly == lz else "x".join(str(d) for d in dims)
@@ -84,9 +85,10 @@ def parse():
     ap.add_argument("--rate", type=float, default=0.0,
                     help="c5: offered rate at --load in requests/s (0: --load x saturation)")
     ap.add_argument("--sessions", type=int, default=2, help="c5: batch sessions per gauge field")
-    ap.add_argument("--group-max-vh", type=int, default=20736,
+    ap.add_argument("--group-max-vh", type=int, default=0,
                     help="c5: lattices of at most this many sites per parity are served by "
-                         "lattice-group sessions (0: every lattice by per-field batch sessions)")
+                         "lattice-group sessions (0: every lattice by per-field batch sessions, "
+                         "measured the better p50 / p99 and throughput at 1000 requests)")
     ap.add_argument("--group-slots", type=int, default=8, help="c5: systems per lattice group")
     ap.add_argument("--max-groups", type=int, default=2, help="c5: lattice-group sessions")
     ap.add_argument("--chunk", type=int, default=16,
@@ -200,7 +202,8 @@ def measured_hbm():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("dslash.cu", "dslash_fx16.cu", "stg_common.cuh", "stg_internal.h", "gauge.cu"):
+    for f in ("dslash.cu", "dslash_fx16.cu", "fx16_pair.cuh", "stg_common.cuh", "stg_internal.h",
+              "gauge.cu"):
         with open(os.path.join(ROOT, "paper_1111_0125_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -494,7 +497,14 @@ def c4_measure(args, steps, warmup, one_by_one_reps=1):
                         "bytes_per_site_per_system": nbytes / vh / n,
                         "achieved": achieved, "peak": peak, "peak_source": src_, "unit": "GB/s",
                         "frac": achieved / peak,
-                        "gflops_576": vh * n * 576 / (t_m / 1000.0) / 1e9},
+                        "gflops_576": vh * n * 576 / (t_m / 1000.0) / 1e9,
+                        # at 16 systems the half-pass is bound by FP32 arithmetic:
+                        # 576 flop per site and system against the FP32 FMA rate
+                        # of 152 SMs x 128 lanes x 2 flop x 2.07 GHz
+                        "alu": {"bound": "alu", "achieved": vh * n * 576 / (t_m / 1000.0) / 1e12,
+                                "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                                "frac": vh * n * 576 / (t_m / 1000.0) / 1e12 / FP32_PEAK_TFLOPS,
+                                "peak_source": "nominal: SM count x FP32 lanes x 2 x max SM clock"}},
         "clocks": ck,
     }
 

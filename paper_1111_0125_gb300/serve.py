@@ -169,6 +169,9 @@ class _Session:
                 with torch.cuda.stream(self.stream):
                     xh = x.to("cpu", non_blocking=True)
                 self.stream.synchronize()
+                # release the slot's device buffers now, before the next
+                # admission allocates its own (the budget counts one pair per slot)
+                del src, x
                 eng._complete(req, status, st, xh.numpy() if eng.keep_solutions else None)
             if done:
                 eng._wake()
@@ -248,6 +251,7 @@ class _GroupSession(_Session):
                 with torch.cuda.stream(self.stream):
                     xh = x.to("cpu", non_blocking=True)
                 self.stream.synchronize()
+                del src, x
                 with eng.lock:
                     entry.in_groups -= 1
                 eng._complete(req, status, st, xh.numpy() if eng.keep_solutions else None)
