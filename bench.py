@@ -23,6 +23,7 @@ and `c5` (a served Poisson stream: saturation, then p50 / p99 at 0.7 of it).
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl stg|reference]
   python bench.py --no-extras                 # c3 only
   python bench.py --workload c4|c5            # the full c4 / c5 runs, own line
+  python bench.py --workload lgroup           # lattice group vs one by one
   python bench.py --kernels-only --reps 3     # kernels alone (for ncu)
 """
 from __future__ import annotations
@@ -75,9 +76,14 @@ def parse():
     ap.add_argument("--kernels", default="all", choices=["all", "sloppy", "f64"],
                     help="--kernels-only: the sloppy-precision Dslash and A, the FP64 Dslash, "
                          "or both")
-    ap.add_argument("--workload", default="c3", choices=["c3", "c4", "c5"],
+    ap.add_argument("--workload", default="c3", choices=["c3", "c4", "c5", "lgroup"],
                     help="c3: 32^3x64 single solve (default); c4: 24^3x48, 16 systems "
-                         "batched; c5: Poisson stream of solve requests (serving)")
+                         "batched; c5: Poisson stream of solve requests (serving); lgroup: "
+                         "systems on several small lattices in one lattice-group session "
+                         "against the same systems solved one by one")
+    ap.add_argument("--lg-lattices", default="8,8,8,8:8;12,12,12,24:8",
+                    help="lgroup: dims:count entries separated by ';' (one gauge field per "
+                         "system)")
     ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--load", type=float, default=0.7,
                     help="c5: offered rate as a fraction of the measured saturation rate")
@@ -705,6 +711,78 @@ def c3_fp16_measure(args, dims, U, b_np):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+def run_lgroup(args):
+    """Several small lattices (each system its own gauge field and size) in
+    one lattice-group session, against the same systems solved one by one
+    with stg_cg_solve; FP32 inner iterations, tol 1e-10."""
+    import numpy as np
+    import torch
+
+    import gen
+    import paper_1111_0125_gb300 as stg
+    torch.cuda.set_device(0)
+    specs = []
+    for ent in args.lg_lattices.split(";"):
+        d, c = ent.split(":")
+        specs += [tuple(int(v) for v in d.split(","))] * int(c)
+    n = len(specs)
+    masses = gen.log_uniform(n, 0.01, 0.1, seed=41)
+    gauges, srcs = [], []
+    for k, dims in enumerate(specs):
+        gauges.append(stg.Gauge(dims, gen.gauge_field(dims, "exp", seed=100 + k, eps=0.5),
+                                sloppy=stg.STG_FP32, recon=12))
+        srcs.append(torch.from_numpy(gen.source(dims, seed=200 + k)).cuda())
+    max_vh = max(g.vh for g in gauges)
+    p = gauges[0].params(sloppy=stg.STG_FP32)
+
+    def grouped():
+        grp = stg.stg_lgroup_create(n, max_vh, stg.STG_FP32, 12, p)
+        xs = [torch.zeros_like(b) for b in srcs]
+        try:
+            for g, b, x, m in zip(gauges, srcs, xs, masses):
+                stg.stg_lgroup_add(grp, g.handle, b, x, m, args.tol)
+            done, nact = [], n
+            while nact:
+                fin, nact = stg.stg_lgroup_step(grp, n)
+                done += fin
+        finally:
+            stg.stg_lgroup_destroy(grp)
+        return done
+
+    def one_by_one():
+        return [stg.stg_cg_solve(g.handle, b, torch.zeros_like(b), m, args.tol, p)
+                for g, b, m in zip(gauges, srcs, masses)]
+
+    for _ in range(args.warmup):
+        grouped()
+        one_by_one()
+    tg, ts = [], []
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        done = grouped()
+        torch.cuda.synchronize()
+        tg.append(time.perf_counter() - t0)
+        t0 = time.perf_counter()
+        single = one_by_one()
+        torch.cuda.synchronize()
+        ts.append(time.perf_counter() - t0)
+    for g in gauges:
+        g.close()
+    t_g, t_s = statistics.median(tg), statistics.median(ts)
+    print(json.dumps({
+        "metric": METRIC, "workload": "lgroup: " + args.lg_lattices + " (one field per system)",
+        "value": n / t_g, "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000.0 * t_g, "higher_is_better": True,
+        "dtype": "f32", "data": "synthetic",
+        "group_ms": 1000.0 * t_g, "one_by_one_ms": 1000.0 * t_s, "speedup": t_s / t_g,
+        "ok": sum(1 for d in done if d[1] == 0), "systems": n,
+        "iters": [d[2]["iters"] for d in sorted(done)],
+        "iters_one_by_one": [s_["iters"] for s_ in single],
+        "true_res_max": max(d[2]["true_res"] for d in done),
+    }), flush=True)
+
+
 def main():
     args = parse()
     dims = tuple(int(v) for v in args.lattice.split(","))
@@ -716,6 +794,9 @@ def main():
         return
     if args.workload == "c5":
         run_c5(args)
+        return
+    if args.workload == "lgroup":
+        run_lgroup(args)
         return
     import numpy as np
     import torch
