@@ -35,3 +35,6 @@ def test_reference_arm_json_line():
         c = pc[name]
         assert c["iters"] > 0 and c["full_solve_s"] > 0 and c["projected_s"] > 0
         assert 0.2 < c["full_over_projected"] < 5.0
+    # one complete solve of the workload, measured
+    fs = d["full_solve"]
+    assert fs["seconds"] > 0 and fs["iters"] > 0 and fs["true_res"] <= 1e-10
