@@ -24,6 +24,7 @@ and `c5` (a served Poisson stream: saturation, then p50 / p99 at 0.7 of it).
   python bench.py --no-extras                 # c3 only
   python bench.py --workload c4|c5            # the full c4 / c5 runs, own line
   python bench.py --workload lgroup           # lattice group vs one by one
+  python bench.py --workload e1               # Dslash on the paper's 28^3x96 lattice
   python bench.py --kernels-only --reps 3     # kernels alone (for ncu)
 """
 from __future__ import annotations
@@ -76,11 +77,12 @@ def parse():
     ap.add_argument("--kernels", default="all", choices=["all", "sloppy", "f64"],
                     help="--kernels-only: the sloppy-precision Dslash and A, the FP64 Dslash, "
                          "or both")
-    ap.add_argument("--workload", default="c3", choices=["c3", "c4", "c5", "lgroup"],
+    ap.add_argument("--workload", default="c3", choices=["c3", "c4", "c5", "lgroup", "e1"],
                     help="c3: 32^3x64 single solve (default); c4: 24^3x48, 16 systems "
                          "batched; c5: Poisson stream of solve requests (serving); lgroup: "
                          "systems on several small lattices in one lattice-group session "
-                         "against the same systems solved one by one")
+                         "against the same systems solved one by one; e1: the Dslash on the "
+                         "paper's 28^3x96 byte-model lattice in FP64/18, FP32/12, FX16/12")
     ap.add_argument("--lg-lattices", default="8,8,8,8:8;12,12,12,24:8",
                     help="lgroup: dims:count entries separated by ';' (one gauge field per "
                          "system)")
@@ -794,6 +796,54 @@ def run_lgroup(args):
     }), flush=True)
 
 
+def run_e1(args):
+    """The Dslash half-pass on 28^3 x 96, the lattice of the paper's byte and
+    flop model (Sec. 2: 1584 B and 576 flop per site in FP64 / 18-real),
+    standalone, back to back on one stream, for FP64/18, FP32/12 and FX16/12:
+    compulsory GB/s against the measured HBM peak, the paper-model
+    "effective" GB/s and GFLOP/s at 576 flop per site."""
+    import torch
+
+    import gen
+    import paper_1111_0125_gb300 as stg
+    from paper_1111_0125_gb300 import model
+    dims = (28, 28, 28, 96)
+    torch.cuda.set_device(0)
+    U = gen.gauge_field(dims, "exp", seed=0, eps=0.6)
+    b = torch.from_numpy(gen.source(dims, seed=1)).cuda()
+    vh = model.even_sites(dims)
+    peak, peak_src = measured_hbm()
+    out = {}
+    for name, prec, recon in (("f64_18", stg.STG_FP64, 18), ("f32_12", stg.STG_FP32, 12),
+                              ("fx16_12", stg.STG_FX16, 12)):
+        with stg.Gauge(dims, U, sloppy=prec, recon=recon) as g:
+            fs = [g.pack(b * (1 + 0.1 * k), prec) for k in range(4)]
+            o = g.new_field(prec)
+            for k in range(5):
+                g.dslash(fs[k % 4], 1, prec, out=o)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 10 if prec == stg.STG_FP64 else 30
+            e0.record()
+            for k in range(reps):
+                g.dslash(fs[k % 4], 1, prec, out=o)
+            e1.record()
+            e1.synchronize()
+            t = e0.elapsed_time(e1) / reps / 1000.0
+        pn = name.split("_")[0]
+        cb = model.compulsory_bytes_per_site(pn, recon) * vh
+        pb = model.paper_bytes_per_site(pn, recon) * vh
+        out[name] = {"us": 1e6 * t, "compulsory_gbs": cb / t / 1e9, "frac": cb / t / 1e9 / peak,
+                     "paper_model_gbs": pb / t / 1e9,
+                     "gflops_576": vh * model.FLOPS_PER_SITE / t / 1e9}
+    print(json.dumps({
+        "metric": METRIC, "workload": "e1: Dslash half-pass on 28^3x96 (the paper's Sec. 2 lattice)",
+        "value": out["fx16_12"]["compulsory_gbs"], "unit": "GB/s", "n_gpus": 1,
+        "higher_is_better": True, "data": "synthetic", "peak": peak, "peak_source": peak_src,
+        "paper_model": {"gflop_per_dslash": vh * model.FLOPS_PER_SITE / 1e9,
+                        "gbyte_per_dslash_f64": model.paper_bytes_per_site("f64", 18) * vh / 1e9},
+        "dslash": out}), flush=True)
+
+
 def main():
     args = parse()
     dims = tuple(int(v) for v in args.lattice.split(","))
@@ -808,6 +858,9 @@ def main():
         return
     if args.workload == "lgroup":
         run_lgroup(args)
+        return
+    if args.workload == "e1":
+        run_e1(args)
         return
     import numpy as np
     import torch
