@@ -25,6 +25,7 @@ and `c5` (a served Poisson stream: saturation, then p50 / p99 at 0.7 of it).
   python bench.py --workload c4|c5            # the full c4 / c5 runs, own line
   python bench.py --workload lgroup           # lattice group vs one by one
   python bench.py --workload e1               # Dslash on the paper's 28^3x96 lattice
+  python bench.py --workload slabs            # t-slab decomposition, Table 1 breakdown
   python bench.py --kernels-only --reps 3     # kernels alone (for ncu)
 """
 from __future__ import annotations
@@ -77,12 +78,14 @@ def parse():
     ap.add_argument("--kernels", default="all", choices=["all", "sloppy", "f64"],
                     help="--kernels-only: the sloppy-precision Dslash and A, the FP64 Dslash, "
                          "or both")
-    ap.add_argument("--workload", default="c3", choices=["c3", "c4", "c5", "lgroup", "e1"],
+    ap.add_argument("--workload", default="c3", choices=["c3", "c4", "c5", "lgroup", "e1", "slabs"],
                     help="c3: 32^3x64 single solve (default); c4: 24^3x48, 16 systems "
                          "batched; c5: Poisson stream of solve requests (serving); lgroup: "
                          "systems on several small lattices in one lattice-group session "
                          "against the same systems solved one by one; e1: the Dslash on the "
-                         "paper's 28^3x96 byte-model lattice in FP64/18, FP32/12, FX16/12")
+                         "paper's 28^3x96 byte-model lattice in FP64/18, FP32/12, FX16/12; slabs: the "
+                         "t-slab decomposition's Dirac operation broken down as in Table 1 "
+                         "(collect, exchange, compute) and its FP64 CG")
     ap.add_argument("--lg-lattices", default="8,8,8,8:8;12,12,12,24:8",
                     help="lgroup: dims:count entries separated by ';' (one gauge field per "
                          "system)")
@@ -844,6 +847,85 @@ def run_e1(args):
         "dslash": out}), flush=True)
 
 
+def run_slabs(args):
+    """The t-slab decomposition on one GPU: one Dirac operation (a Dslash
+    half-pass) of 32^3 x 64 cut into P = 1, 2, 4, 8 slabs, broken down as in
+    Table 1 (boundary collect, exchange, the slabs' Dslash, the whole
+    operation in each schedule), in FP64/18 and FP32/12, beside the
+    undecomposed Dslash of the same lattice; then the FP64 CG of 16^3 x 32
+    (m = 0.01, tol 1e-10) on 4 slabs against the undecomposed FP64 CG."""
+    import torch
+
+    import gen
+    import paper_1111_0125_gb300 as stg
+    from paper_1111_0125_gb300 import model
+    torch.cuda.set_device(0)
+    dims = (32, 32, 32, 64)
+    U = gen.gauge_field(dims, "exp", seed=0, eps=0.6)
+    b = torch.from_numpy(gen.source(dims, seed=1)).cuda()
+    vh = model.even_sites(dims)
+    reps = max(args.reps, 20)
+    table = {}
+    for name, prec, recon in (("f64_18", stg.STG_FP64, 18), ("f32_12", stg.STG_FP32, 12)):
+        with stg.Gauge(dims, U, sloppy=prec, recon=recon) as g:
+            f = g.pack(b, prec)
+            o = g.new_field(prec)
+            for _ in range(3):
+                g.dslash(f, 1, prec, out=o)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                g.dslash(f, 1, prec, out=o)
+            e1.record()
+            e1.synchronize()
+            whole_us = 1e3 * e0.elapsed_time(e1) / reps
+        row = {"undecomposed_us": whole_us, "slabs": {}}
+        for P in (1, 2, 4, 8):
+            h = stg.stg_slabs_create(dims, U, P, prec, recon)
+            try:
+                stg.stg_slabs_load(h, 0, b)
+                r = {"face_bytes": vh // 64 * {stg.STG_FP64: 48, stg.STG_FP32: 24}[prec]}
+                for mode, mname in ((stg.STG_SLAB_COPY, "copy"), (stg.STG_SLAB_DIRECT, "direct")):
+                    for ov in (0, 1):
+                        stg.stg_slabs_set_exchange(h, mode, ov)
+                        t = stg.stg_slabs_profile(h, reps)
+                        key = mname + ("_overlap" if ov else "")
+                        r[key] = {k[:-3] + "_us": 1e3 * v for k, v in t.items()}
+                torch.cuda.synchronize()
+            finally:
+                stg.stg_slabs_destroy(h)
+            row["slabs"][str(P)] = r
+        table[name] = row
+    # FP64 CG on 4 slabs against the undecomposed FP64 CG
+    cdims, mass, tol = (16, 16, 16, 32), 0.01, 1e-10
+    Uc = gen.gauge_field(cdims, "exp", seed=0, eps=0.4)
+    bc = torch.from_numpy(gen.source(cdims, seed=1)).cuda()
+    cg = {}
+    with stg.Gauge(cdims, Uc, sloppy=stg.STG_FP64, recon=18) as g:
+        p64 = g.params(policy=stg.STG_CG_PLAIN, sloppy=stg.STG_FP64)
+        g.cg_solve(bc, mass, tol, p64)
+        _, st = g.cg_solve(bc, mass, tol, p64)
+        cg["undecomposed"] = {"seconds": st["seconds"], "iters": st["iters"], "true_res": st["true_res"]}
+    for P, mode, ov in ((4, stg.STG_SLAB_COPY, 0), (4, stg.STG_SLAB_DIRECT, 1)):
+        h = stg.stg_slabs_create(cdims, Uc, P, stg.STG_FP64, 18)
+        try:
+            stg.stg_slabs_set_exchange(h, mode, ov)
+            x = torch.zeros_like(bc)
+            stg.stg_slabs_cg_solve(h, bc, x, mass, tol)
+            x = torch.zeros_like(bc)
+            st = stg.stg_slabs_cg_solve(h, bc, x, mass, tol)
+        finally:
+            stg.stg_slabs_destroy(h)
+        cg[f"{P}_slabs_{'direct_overlap' if ov else 'copy'}"] = {
+            "seconds": st["seconds"], "iters": st["iters"], "true_res": st["true_res"],
+            "launches": st["launches"]}
+    print(json.dumps({
+        "metric": METRIC, "workload": "slabs: t-slab decomposition of 32^3x64 on one GPU "
+        "(Table 1 breakdown per Dirac operation); FP64 CG of 16^3x32 on 4 slabs",
+        "unit": "us per Dirac operation", "n_gpus": 1, "data": "synthetic",
+        "reps": reps, "dirac": table, "cg": cg}), flush=True)
+
+
 def main():
     args = parse()
     dims = tuple(int(v) for v in args.lattice.split(","))
@@ -861,6 +943,9 @@ def main():
         return
     if args.workload == "e1":
         run_e1(args)
+        return
+    if args.workload == "slabs":
+        run_slabs(args)
         return
     import numpy as np
     import torch

@@ -414,6 +414,71 @@ stg_status stg_cg_solve(const stg_gauge *g, const double *src_dev, double *x_dev
                         double mass, double tol, const stg_cg_params *params,
                         stg_cg_stats *stats, stg_stream_t stream);
 
+/*
+ * t-slab domain decomposition (Sec. 3.3 and Table 1), all slabs on the
+ * current device.  The lattice is cut along t into nslabs slabs of Lt /
+ * nslabs time slices; each slab keeps its own links, fields and face buffers,
+ * as one rank of a multi-GPU run does.  One Dirac operation (a Dslash half-
+ * pass) is the paper's sequence: boundary collect (a kernel gathers each
+ * slab's first and last time slice of the input field into face buffers),
+ * exchange (each face reaches the neighbouring slab's ghost buffer), and the
+ * Dslash of every slab, whose t-hops out of the slab read the ghosts.  The
+ * backward t-links of a slab's first slice live on the previous slab; they
+ * are constant and are copied in once, at creation.  Global sums (d^dag A d,
+ * |r|^2) are formed per slab and added in slab order: the two-scalar
+ * allreduce of a multi-GPU CG.  There is no transport between GPUs here.
+ *
+ *   stg_slabs_create: dims as for stg_gauge_create (all even, > 0); nslabs
+ *     1..64 with Lt % nslabs == 0 and Lt / nslabs even (STG_ERR_DIMS
+ *     otherwise, before any device work); prec / recon the links' storage
+ *     (any precision; 12 or 18); links_host as for stg_gauge_create.  Returns
+ *     after the upload and packing are complete.
+ *   stg_slabs_set_exchange: mode STG_SLAB_COPY (collect into each slab's
+ *     send buffers, then one device-to-device copy per face: the message of a
+ *     multi-GPU run) or STG_SLAB_DIRECT (the collect kernel stores straight
+ *     into the neighbours' ghost buffers, as through peer pointers);
+ *     overlap = 1 runs the interior time slices (1 .. Lt/nslabs - 2) on the
+ *     caller's stream while collect and exchange run on a second stream,
+ *     then the two boundary slices (Sec. 4's overlap of communication with
+ *     computation).  Results are bitwise the same in every mode.
+ *   Field slots: each slab holds STG_SLAB_SLOTS fields in `prec` (slots 0..5;
+ *     stg_slabs_cg_solve uses all of them).  stg_slabs_load packs a canonical
+ *     complex128 [Vh][3] device field of one parity (the global lattice's
+ *     checkerboard order, t slowest) into slot `slot` of every slab;
+ *     stg_slabs_store writes a slot back in the same form.
+ *   stg_slabs_dslash: slot out = D slot in (Eq. 5) with output parity
+ *     out_parity (the slot contents are one parity; slots carry no parity).
+ *   stg_slabs_apply_A_dot: slot out = A slot in (Eq. 3, via slot 4 as the
+ *     odd intermediate) and *dot_dev (device double) = Re sum in^dag out.
+ *   stg_slabs_cg_solve: CG of Fig. 1 in FP64 on the decomposed operator
+ *     (prec must be STG_FP64: else STG_ERR_UNSUPPORTED), stopping at
+ *     |b - A x| <= tol |b| with the true residual recomputed at the end
+ *     (restarts from it otherwise, like stg_cg_solve's FP64 policy);
+ *     src_dev / x_dev canonical [Vh][3] device fields, x_dev holding x0 on
+ *     entry; maxiter 0 = 10 N_dim.  Synchronises `stream`.
+ *   stg_slabs_profile: one Dirac operation (out parity 1, slot 0 -> slot 4),
+ *     `reps` times each: ms[0] the collect kernel, ms[1] the exchange copies
+ *     (0 in DIRECT mode), ms[2] the slabs' Dslash kernels, ms[3] the whole
+ *     operation in the current mode; means per operation from CUDA events.
+ *   stg_slabs_bytes: device bytes a handle of this shape allocates.
+ */
+typedef struct stg_slabs stg_slabs;
+enum { STG_SLAB_COPY = 0, STG_SLAB_DIRECT = 1, STG_SLAB_SLOTS = 6 };
+stg_status stg_slabs_create(const int dims[4], const double *links_host, int nslabs, stg_prec prec,
+                            int recon, stg_stream_t stream, stg_slabs **out);
+stg_status stg_slabs_destroy(stg_slabs *s);
+stg_status stg_slabs_set_exchange(stg_slabs *s, int mode, int overlap);
+stg_status stg_slabs_load(stg_slabs *s, int slot, const double *canon_dev, stg_stream_t stream);
+stg_status stg_slabs_store(stg_slabs *s, int slot, double *canon_dev, stg_stream_t stream);
+stg_status stg_slabs_dslash(stg_slabs *s, int out_parity, int in_slot, int out_slot,
+                            stg_stream_t stream);
+stg_status stg_slabs_apply_A_dot(stg_slabs *s, double mass, int in_slot, int out_slot, double *dot_dev,
+                                 stg_stream_t stream);
+stg_status stg_slabs_cg_solve(stg_slabs *s, const double *src_dev, double *x_dev, double mass,
+                              double tol, long maxiter, stg_cg_stats *stats, stg_stream_t stream);
+stg_status stg_slabs_profile(stg_slabs *s, int reps, double ms[4], stg_stream_t stream);
+size_t stg_slabs_bytes(const int dims[4], int nslabs, stg_prec prec, int recon);
+
 #ifdef __cplusplus
 }
 #endif

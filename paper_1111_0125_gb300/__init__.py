@@ -102,6 +102,16 @@ def _load():
         "stg_lgroup_add": (i, [p, p, p, p, d, d, p]),
         "stg_lgroup_step": (i, [p, i, p, p, p, p, p]),
         "stg_lgroup_bytes": (sz, [i, ctypes.c_long, i]),
+        "stg_slabs_create": (i, [p, p, i, i, i, p, p]),
+        "stg_slabs_destroy": (i, [p]),
+        "stg_slabs_set_exchange": (i, [p, i, i]),
+        "stg_slabs_load": (i, [p, i, p, p]),
+        "stg_slabs_store": (i, [p, i, p, p]),
+        "stg_slabs_dslash": (i, [p, i, i, i, p]),
+        "stg_slabs_apply_A_dot": (i, [p, d, i, i, p, p]),
+        "stg_slabs_cg_solve": (i, [p, p, p, d, d, ctypes.c_long, p, p]),
+        "stg_slabs_profile": (i, [p, i, p, p]),
+        "stg_slabs_bytes": (sz, [p, i, i, i]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -348,6 +358,71 @@ def stg_lgroup_step(group: int, max_done: int = 16):
 
 def stg_lgroup_bytes(max_systems: int, max_vh: int, sloppy: int) -> int:
     return int(lib.stg_lgroup_bytes(int(max_systems), int(max_vh), int(sloppy)))
+
+
+STG_SLAB_COPY, STG_SLAB_DIRECT, STG_SLAB_SLOTS = 0, 1, 6
+
+
+def stg_slabs_create(dims, links_host: np.ndarray, nslabs: int, prec: int = STG_FP64,
+                     recon: int = 18, stream=None) -> int:
+    """t-slab decomposition of the lattice into nslabs slabs on the current
+    device; canonical complex128 links as for stg_gauge_create (host)."""
+    dd = (ctypes.c_int * 4)(*[int(v) for v in dims])
+    links = np.ascontiguousarray(links_host, dtype=np.complex128)
+    lx, ly, lz, lt = (int(v) for v in dims)
+    if links.size != lx * ly * lz * lt * 4 * 9:
+        raise ValueError("links_host must hold Lt*Lz*Ly*Lx*4*3*3 complex entries")
+    h = ctypes.c_void_p()
+    _check(lib.stg_slabs_create(dd, links.ctypes.data, int(nslabs), int(prec), int(recon),
+                                _stream(stream), ctypes.byref(h)), "stg_slabs_create")
+    return h.value
+
+
+def stg_slabs_destroy(h: int) -> None:
+    lib.stg_slabs_destroy(h)
+
+
+def stg_slabs_set_exchange(h: int, mode: int, overlap: int) -> None:
+    _check(lib.stg_slabs_set_exchange(h, int(mode), int(overlap)), "stg_slabs_set_exchange")
+
+
+def stg_slabs_load(h: int, slot: int, canon_dev, stream=None) -> None:
+    _check(lib.stg_slabs_load(h, int(slot), _ptr(canon_dev), _stream(stream)), "stg_slabs_load")
+
+
+def stg_slabs_store(h: int, slot: int, canon_dev, stream=None) -> None:
+    _check(lib.stg_slabs_store(h, int(slot), _ptr(canon_dev), _stream(stream)), "stg_slabs_store")
+
+
+def stg_slabs_dslash(h: int, out_parity: int, in_slot: int, out_slot: int, stream=None) -> None:
+    _check(lib.stg_slabs_dslash(h, int(out_parity), int(in_slot), int(out_slot), _stream(stream)),
+           "stg_slabs_dslash")
+
+
+def stg_slabs_apply_A_dot(h: int, mass: float, in_slot: int, out_slot: int, dot_dev,
+                          stream=None) -> None:
+    _check(lib.stg_slabs_apply_A_dot(h, float(mass), int(in_slot), int(out_slot), _ptr(dot_dev),
+                                     _stream(stream)), "stg_slabs_apply_A_dot")
+
+
+def stg_slabs_cg_solve(h: int, src_dev, x_dev, mass: float, tol: float, maxiter: int = 0,
+                       stream=None) -> dict:
+    st = stg_cg_stats()
+    rc = lib.stg_slabs_cg_solve(h, _ptr(src_dev), _ptr(x_dev), float(mass), float(tol),
+                                int(maxiter), ctypes.byref(st), _stream(stream))
+    _check(rc, "stg_slabs_cg_solve", st.as_dict())
+    return st.as_dict()
+
+
+def stg_slabs_profile(h: int, reps: int = 20, stream=None) -> dict:
+    ms = (ctypes.c_double * 4)()
+    _check(lib.stg_slabs_profile(h, int(reps), ms, _stream(stream)), "stg_slabs_profile")
+    return {"collect_ms": ms[0], "exchange_ms": ms[1], "compute_ms": ms[2], "total_ms": ms[3]}
+
+
+def stg_slabs_bytes(dims, nslabs: int, prec: int, recon: int) -> int:
+    d = (ctypes.c_int * 4)(*[int(v) for v in dims])
+    return int(lib.stg_slabs_bytes(d, int(nslabs), int(prec), int(recon)))
 
 
 def stg_gauge_bytes(dims, sloppy: int, recon: int) -> int:

@@ -34,8 +34,11 @@ Geom make_geom(const int dims[4])
 // ---------------------------------------------------------------------------
 // link packing: one thread per (site, mu) of the canonical array
 // ---------------------------------------------------------------------------
+// t_flip: the time slice whose forward t-links carry the antiperiodic sign
+// (Lt - 1 for a whole lattice; for a t-slab, its last slice when the slab
+// holds global t = Lt - 1, else -1: none)
 template <int P, int R>
-__global__ void k_pack_links(Geom g, const double2 *__restrict__ ucan, char *base, size_t blk_bytes)
+__global__ void k_pack_links(Geom g, const double2 *__restrict__ ucan, char *base, size_t blk_bytes, int t_flip)
 {
     const long n = (long)g.Vh * 2 * 4;
     const long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -54,7 +57,7 @@ __global__ void k_pack_links(Geom g, const double2 *__restrict__ ucan, char *bas
     if (mu >= 2) e += y;
     if (mu >= 3) e += z;
     double s = (e & 1) ? -1.0 : 1.0;
-    if (mu == 3 && t == g.L[3] - 1) s = -s;
+    if (mu == 3 && t == t_flip) s = -s;
     const double2 *src = ucan + (size_t)k * 9;
     double2 u[9];
 #pragma unroll
@@ -127,8 +130,8 @@ __global__ void k_pack_links(Geom g, const double2 *__restrict__ ucan, char *bas
     }
 }
 
-static stg_status pack_links(const Geom &g, const double2 *ucan, int prec, int recon,
-                             LinkField *lf, cudaStream_t s)
+stg_status pack_links_flip(const Geom &g, const double2 *ucan, int prec, int recon, int t_flip,
+                           LinkField *lf, cudaStream_t s)
 {
     lf->prec = prec;
     lf->recon = recon;
@@ -141,7 +144,7 @@ static stg_status pack_links(const Geom &g, const double2 *ucan, int prec, int r
     }
     const long n = (long)g.Vh * 8;
     const int grid = (int)((n + 255) / 256);
-#define STG_PACK(P_, R_) k_pack_links<P_, R_><<<grid, 256, 0, s>>>(g, ucan, lf->base, lf->blk_bytes)
+#define STG_PACK(P_, R_) k_pack_links<P_, R_><<<grid, 256, 0, s>>>(g, ucan, lf->base, lf->blk_bytes, t_flip)
     if (prec == P64) { if (recon == 18) STG_PACK(P64, 18); else STG_PACK(P64, 12); }
     else if (prec == P32) { if (recon == 18) STG_PACK(P32, 18); else STG_PACK(P32, 12); }
     else if (prec == P16) { if (recon == 18) STG_PACK(P16, 18); else STG_PACK(P16, 12); }
@@ -150,6 +153,12 @@ static stg_status pack_links(const Geom &g, const double2 *ucan, int prec, int r
 #undef STG_PACK
     STG_CUDA(cudaGetLastError());
     return STG_OK;
+}
+
+static stg_status pack_links(const Geom &g, const double2 *ucan, int prec, int recon,
+                             LinkField *lf, cudaStream_t s)
+{
+    return pack_links_flip(g, ucan, prec, recon, g.L[3] - 1, lf, s);
 }
 
 // Tile-major copy of FX16 / 12-real links (see kFxTile): one thread per

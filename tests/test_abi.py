@@ -142,3 +142,26 @@ def test_lattice_group_host_checks(stg):
     with pytest.raises(stg.StgError) as e:
         stg.stg_lgroup_create(4, 128, 9, 12, stream=0)
     assert e.value.status == stg.STG_ERR_INVALID_ARG
+
+
+def test_slab_decomposition_host_checks(stg):
+    # rejected before any CUDA call
+    U = np.zeros(4 * 4 * 4 * 8 * 36, dtype=np.complex128)
+    for nslabs in (0, 3, 8, 65):  # 3 does not divide 8; 8 slabs would be one slice thick
+        with pytest.raises(stg.StgError) as e:
+            stg.stg_slabs_create((4, 4, 4, 8), U, nslabs, stg.STG_FP64, 18, stream=0)
+        assert e.value.status == stg.STG_ERR_DIMS
+    for prec, recon in [(9, 18), (stg.STG_FP64, 10)]:
+        with pytest.raises(stg.StgError) as e:
+            stg.stg_slabs_create((4, 4, 4, 8), U, 2, prec, recon, stream=0)
+        assert e.value.status == stg.STG_ERR_INVALID_ARG
+    assert stg.stg_slabs_bytes((4, 4, 4, 8), 3, stg.STG_FP64, 18) == 0
+    assert stg.stg_slabs_bytes((4, 4, 4, 8), 8, stg.STG_FP64, 18) == 0
+    # links, ghost links, six field slots, four faces per slab: the byte count
+    # grows with the slab count only through the per-slab face and ghost terms
+    one = stg.stg_slabs_bytes((8, 8, 8, 16), 1, stg.STG_FP64, 18)
+    four = stg.stg_slabs_bytes((8, 8, 8, 16), 4, stg.STG_FP64, 18)
+    vh = 8 * 8 * 8 * 16 // 2
+    assert one >= vh * (8 * 144 + 6 * 48)
+    assert four > one
+    assert four - one < 4 * 2 * (256 * 144 + 4 * 256 * 48) + 8 * 4096
