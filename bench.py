@@ -852,8 +852,9 @@ def run_slabs(args):
     half-pass) of 32^3 x 64 cut into P = 1, 2, 4, 8 slabs, broken down as in
     Table 1 (boundary collect, exchange, the slabs' Dslash, the whole
     operation in each schedule), in FP64/18 and FP32/12, beside the
-    undecomposed Dslash of the same lattice; then the FP64 CG of 16^3 x 32
-    (m = 0.01, tol 1e-10) on 4 slabs against the undecomposed FP64 CG."""
+    undecomposed Dslash of the same lattice; then the CG of 16^3 x 32 (m =
+    0.01, tol 1e-10) on 4 slabs against the undecomposed solver, in FP64 and
+    with FP32 / 12-real inner iterations and FP64 reliable updates."""
     import torch
 
     import gen
@@ -919,9 +920,26 @@ def run_slabs(args):
         cg[f"{P}_slabs_{'direct_overlap' if ov else 'copy'}"] = {
             "seconds": st["seconds"], "iters": st["iters"], "true_res": st["true_res"],
             "launches": st["launches"]}
+    # mixed precision: FP32 / 12-real inner iterations, FP64 reliable updates
+    with stg.Gauge(cdims, Uc, sloppy=stg.STG_FP32, recon=12) as g:
+        g.cg_solve(bc, mass, tol)
+        _, st = g.cg_solve(bc, mass, tol)
+        cg["mixed_f32_12_undecomposed"] = {"seconds": st["seconds"], "iters": st["iters"],
+                                           "updates": st["updates"], "true_res": st["true_res"]}
+    h = stg.stg_slabs_create(cdims, Uc, 4, stg.STG_FP32, 12)
+    try:
+        stg.stg_slabs_set_exchange(h, stg.STG_SLAB_DIRECT, 0)
+        x = torch.zeros_like(bc)
+        stg.stg_slabs_cg_solve(h, bc, x, mass, tol)
+        x = torch.zeros_like(bc)
+        st = stg.stg_slabs_cg_solve(h, bc, x, mass, tol)
+    finally:
+        stg.stg_slabs_destroy(h)
+    cg["mixed_f32_12_4_slabs_direct"] = {"seconds": st["seconds"], "iters": st["iters"],
+                                         "updates": st["updates"], "true_res": st["true_res"]}
     print(json.dumps({
         "metric": METRIC, "workload": "slabs: t-slab decomposition of 32^3x64 on one GPU "
-        "(Table 1 breakdown per Dirac operation); FP64 CG of 16^3x32 on 4 slabs",
+        "(Table 1 breakdown per Dirac operation); FP64 and mixed CG of 16^3x32 on 4 slabs",
         "unit": "us per Dirac operation", "n_gpus": 1, "data": "synthetic",
         "reps": reps, "dirac": table, "cg": cg}), flush=True)
 

@@ -442,7 +442,7 @@ stg_status stg_cg_solve(const stg_gauge *g, const double *src_dev, double *x_dev
  *     then the two boundary slices (Sec. 4's overlap of communication with
  *     computation).  Results are bitwise the same in every mode.
  *   Field slots: each slab holds STG_SLAB_SLOTS fields in `prec` (slots 0..5;
- *     stg_slabs_cg_solve uses all of them).  stg_slabs_load packs a canonical
+ *     stg_slabs_cg_solve overwrites them).  stg_slabs_load packs a canonical
  *     complex128 [Vh][3] device field of one parity (the global lattice's
  *     checkerboard order, t slowest) into slot `slot` of every slab;
  *     stg_slabs_store writes a slot back in the same form.
@@ -450,12 +450,16 @@ stg_status stg_cg_solve(const stg_gauge *g, const double *src_dev, double *x_dev
  *     out_parity (the slot contents are one parity; slots carry no parity).
  *   stg_slabs_apply_A_dot: slot out = A slot in (Eq. 3, via slot 4 as the
  *     odd intermediate) and *dot_dev (device double) = Re sum in^dag out.
- *   stg_slabs_cg_solve: CG of Fig. 1 in FP64 on the decomposed operator
- *     (prec must be STG_FP64: else STG_ERR_UNSUPPORTED), stopping at
- *     |b - A x| <= tol |b| with the true residual recomputed at the end
- *     (restarts from it otherwise, like stg_cg_solve's FP64 policy);
- *     src_dev / x_dev canonical [Vh][3] device fields, x_dev holding x0 on
- *     entry; maxiter 0 = 10 N_dim.  Synchronises `stream`.
+ *   stg_slabs_cg_solve: CG on the decomposed operator, stopping at
+ *     |b - A x| <= tol |b| in FP64.  FP64 slabs: Fig. 1 in FP64, the true
+ *     residual recomputed at the end (restarting from it otherwise).  FP32 /
+ *     FX16 slabs: inner iterations in that precision (y and r in FP32) with
+ *     the reliable updates of Sec. 3.2 (x += y, r = b - A x with an FP64 /
+ *     18-real copy of the links that the handle then keeps) and the restart
+ *     of Eq. 6, delta = 0.05 (FP32) or 0.25 (FX16); FP16 / BF16 slabs:
+ *     STG_ERR_UNSUPPORTED.  src_dev / x_dev canonical [Vh][3] device fields,
+ *     x_dev holding x0 on entry; maxiter 0 = 10 N_dim.  Synchronises
+ *     `stream`.
  *   stg_slabs_profile: one Dirac operation (out parity 1, slot 0 -> slot 4),
  *     `reps` times each: ms[0] the collect kernel, ms[1] the exchange copies
  *     (0 in DIRECT mode), ms[2] the slabs' Dslash kernels, ms[3] the whole

@@ -53,9 +53,17 @@ stg_status unpack_field(const Geom &g, int prec, const void *in, double *canon, 
 stg_status pack_links_flip(const Geom &g, const double2 *ucan, int prec, int recon, int t_flip,
                            LinkField *lf, cudaStream_t s);
 
-constexpr int kSlabSlots = STG_SLAB_SLOTS;
+// Field slots of every slab, each sized for FP64 (48 bytes per site): the
+// user's six (slots 0-5 in the handle's precision), then four FP64 vectors
+// of the CG.  The CG's inner vectors live in the user slots: y and r in PR,
+// d, t and q in the handle's precision PD.
+constexpr int kUserSlots = STG_SLAB_SLOTS;
+constexpr int kSlabSlots = kUserSlots + 4;
 constexpr int kMaxSlabs = 64;
-enum SlabSlot { SL_B = 0, SL_X = 1, SL_R = 2, SL_D = 3, SL_T = 4, SL_Q = 5 };
+enum SlabSlot { SL_Y = 1, SL_R = 2, SL_D = 3, SL_T = 4, SL_Q = 5, SL_B64 = 6, SL_X64 = 7, SL_R64 = 8, SL_T64 = 9 };
+
+// the precision of y and r for inner iterations in PD
+static int slab_pr(int pd) { return pd == P64 ? P64 : P32; }
 
 static size_t sl_align(size_t n) { return (n + 255) & ~(size_t)255; }
 
@@ -92,6 +100,8 @@ static int link_planes(int prec, int recon, int e[9])
 struct SlabDev {
     const char *lk[8];        // link blocks, index parity * 4 + mu
     const char *ghost_lk[2];  // per output parity: U_t(x - t) of the sites at slice 0 (planes of stride st)
+    const char *lk64[8];      // the FP64 / 18-real links of the CG's true residual (= lk for FP64 handles)
+    const char *ghost64[2];
     char *slot[kSlabSlots];   // fields (planes of stride Vh)
     char *send[2];            // COPY mode: [0] slice 0, [1] slice Lts - 1 of the collected field
     char *recv[2];            // ghosts: [0] next slab's slice 0, [1] previous slab's slice Lts - 1
@@ -110,6 +120,8 @@ struct SlabArgs {
     int pstride, pbase;       // partial index of this launch's block 0
     int part;                 // 0: interior slices, 1: the two boundary slices, 2: both
     int nb_int;               // blocks of the interior part (part 2: blocks below it are interior)
+    int prec, recon;          // the operator's storage
+    int hi;                   // 1: the FP64 / 18-real link set (lk64, ghost64)
 };
 
 // The slab's entry, staged in shared memory once per block (every thread of
@@ -166,8 +178,9 @@ __global__ void __launch_bounds__(kBlock) k_slab_collect(const CollectArgs a)
 // order as dslash_site, with the t-hops across a slab edge on the ghosts
 // ---------------------------------------------------------------------------
 template <int P, int R>
-__device__ __forceinline__ Vec3<typename Real<P>::T> slab_site(const Geom &g, const SlabDev *S, int parity,
-                                                               const void *in, int i)
+__device__ __forceinline__ Vec3<typename Real<P>::T> slab_site(const Geom &g, const SlabDev *S,
+                                                               const char *const *lk, const char *const *gl,
+                                                               int parity, const void *in, int i)
 {
     typedef typename Real<P>::T T;
     const int vh = g.Vh, st = g.st, top = g.L[3] - 1;
@@ -193,12 +206,12 @@ __device__ __forceinline__ Vec3<typename Real<P>::T> slab_site(const Geom &g, co
         }
         const T s2f = (R == 12) ? T(sf * LinkPost<P>::row2) : T(1);
         const T s2b = (R == 12) ? T(sb * LinkPost<P>::row2) : T(1);
-        const Mat3<T> uf = LinkIO<P, R>::load(S->lk[parity * 4 + mu], vh, i);
+        const Mat3<T> uf = LinkIO<P, R>::load(lk[parity * 4 + mu], vh, i);
         const Vec3<T> vf = up ? FieldIO<P>::load_nc(S->recv[0], st, i - top * st)
                               : FieldIO<P>::load_nc(in, vh, jf);
         mul_add<R == 12>(uf, vf, acc, s2f);
-        const Mat3<T> ub = down ? LinkIO<P, R>::load(S->ghost_lk[parity], st, i)
-                                : LinkIO<P, R>::load(S->lk[(1 - parity) * 4 + mu], vh, jb);
+        const Mat3<T> ub = down ? LinkIO<P, R>::load(gl[parity], st, i)
+                                : LinkIO<P, R>::load(lk[(1 - parity) * 4 + mu], vh, jb);
         const Vec3<T> vb = down ? FieldIO<P>::load_nc(S->recv[1], st, i) : FieldIO<P>::load_nc(in, vh, jb);
         adj_mul_sub(ub, vb, acc, s2b);
     }
@@ -242,7 +255,8 @@ __global__ void __launch_bounds__(kBlock) k_slab_dslash(const SlabArgs a)
     }
     double dot = 0.0;
     if (ok) {
-        const Vec3<T> acc = slab_site<P, R>(a.g, S, a.parity, S->slot[a.in], i);
+        const Vec3<T> acc = slab_site<P, R>(a.g, S, a.hi ? S->lk64 : S->lk, a.hi ? S->ghost64 : S->ghost_lk,
+                                            a.parity, S->slot[a.in], i);
         void *out = S->slot[a.out];
         if (EPI == EPI_NONE || EPI == EPI_GATE) {
             FieldIO<P>::store(out, vh, i, acc);
@@ -285,34 +299,47 @@ __global__ void __launch_bounds__(kBlock) k_slab_dslash(const SlabArgs a)
 }
 
 // ---------------------------------------------------------------------------
-// CG vector kernels on the slabs (FP64, one site per thread, blockIdx.y =
-// slab) and the slab-ordered sums
+// CG vector kernels on the slabs (one site per thread, blockIdx.y = slab;
+// slots as in SlabSlot) and the slab-ordered sums
 // ---------------------------------------------------------------------------
-// x += alpha d, r -= alpha q, |r|^2 partials (Fig. 1)
-__global__ void __launch_bounds__(kBlock) k_slab_update(const SlabArgs a)
+struct VecArgs {
+    const SlabDev *sl;
+    int vh;
+    CGState *state;
+    double *partials;
+    int pstride;
+};
+
+// y += alpha d, r -= alpha q, |r|^2 partials (Fig. 1)
+template <int PD, int PR>
+__global__ void __launch_bounds__(kBlock) k_slab_update(const VecArgs a)
 {
     const CGState *st = a.state;
     if (st->flag != FLAG_RUN) return;
+    typedef typename Real<PR>::T T;
     const SlabDev *S = a.sl + blockIdx.y;
-    const int vh = a.g.Vh;
+    const int vh = a.vh;
     const int i = blockIdx.x * kBlock + threadIdx.x;
     double n = 0.0;
     if (i < vh) {
-        const double alpha = st->alpha;
-        const Vec3<double> d = FieldIO<P64>::load(S->slot[SL_D], vh, i);
-        const Vec3<double> q = FieldIO<P64>::load(S->slot[SL_Q], vh, i);
-        Vec3<double> x = FieldIO<P64>::load(S->slot[SL_X], vh, i);
-        Vec3<double> r = FieldIO<P64>::load(S->slot[SL_R], vh, i);
+        const T alpha = T(st->alpha);
+        const auto d = FieldIO<PD>::load(S->slot[SL_D], vh, i);
+        const auto q = FieldIO<PD>::load(S->slot[SL_Q], vh, i);
+        Vec3<T> y = FieldIO<PR>::load(S->slot[SL_Y], vh, i);
+        Vec3<T> r = FieldIO<PR>::load(S->slot[SL_R], vh, i);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            x.r[c] += alpha * d.r[c];
-            x.i[c] += alpha * d.i[c];
-            r.r[c] -= alpha * q.r[c];
-            r.i[c] -= alpha * q.i[c];
-            n += r.r[c] * r.r[c] + r.i[c] * r.i[c];
+            y.r[c] += alpha * T(d.r[c]);
+            y.i[c] += alpha * T(d.i[c]);
+            r.r[c] -= alpha * T(q.r[c]);
+            r.i[c] -= alpha * T(q.i[c]);
         }
-        FieldIO<P64>::store(S->slot[SL_X], vh, i, x);
-        FieldIO<P64>::store(S->slot[SL_R], vh, i, r);
+        FieldIO<PR>::store(S->slot[SL_Y], vh, i, y);
+        const Vec3<T> rs = FieldIO<PR>::store(S->slot[SL_R], vh, i, r);
+        T m = T(0);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) m += rs.r[c] * rs.r[c] + rs.i[c] * rs.i[c];
+        n = double(m);
     }
     __shared__ double sm[32];
     const double b = block_sum<kBlock>(n, sm);
@@ -320,35 +347,95 @@ __global__ void __launch_bounds__(kBlock) k_slab_update(const SlabArgs a)
 }
 
 // d = r + beta d
-__global__ void __launch_bounds__(kBlock) k_slab_xpay(const SlabArgs a)
+template <int PD, int PR>
+__global__ void __launch_bounds__(kBlock) k_slab_xpay(const VecArgs a)
 {
     const CGState *st = a.state;
     if (st->flag != FLAG_RUN) return;
+    typedef typename Real<PR>::T T;
+    typedef typename Real<PD>::T TD;
     const SlabDev *S = a.sl + blockIdx.y;
-    const int vh = a.g.Vh;
+    const int vh = a.vh;
     const int i = blockIdx.x * kBlock + threadIdx.x;
     if (i >= vh) return;
-    const double beta = st->beta;
-    const Vec3<double> r = FieldIO<P64>::load(S->slot[SL_R], vh, i);
-    Vec3<double> d = FieldIO<P64>::load(S->slot[SL_D], vh, i);
+    const T beta = T(st->beta);
+    const Vec3<T> r = FieldIO<PR>::load(S->slot[SL_R], vh, i);
+    const auto d = FieldIO<PD>::load(S->slot[SL_D], vh, i);
+    Vec3<TD> o;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        d.r[c] = r.r[c] + beta * d.r[c];
-        d.i[c] = r.i[c] + beta * d.i[c];
+        o.r[c] = TD(r.r[c] + beta * T(d.r[c]));
+        o.i[c] = TD(r.i[c] + beta * T(d.i[c]));
     }
-    FieldIO<P64>::store(S->slot[SL_D], vh, i, d);
+    FieldIO<PD>::store(S->slot[SL_D], vh, i, o);
 }
 
-// slot out = slot in (FP64), and |in|^2 partials
-__global__ void __launch_bounds__(kBlock) k_slab_copy_norm(const SlabArgs a)
+// start or restart of the inner iteration (Fig. 2, Eq. 6): y = 0, r = r64 in
+// PR, d = r + beta d (beta = 0: d = r)
+template <int PD, int PR>
+__global__ void __launch_bounds__(kBlock) k_slab_reset(const VecArgs a, double beta)
+{
+    typedef typename Real<PR>::T T;
+    typedef typename Real<PD>::T TD;
+    const SlabDev *S = a.sl + blockIdx.y;
+    const int vh = a.vh;
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= vh) return;
+    const Vec3<double> r64 = FieldIO<P64>::load(S->slot[SL_R64], vh, i);
+    Vec3<T> r, z;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        r.r[c] = T(r64.r[c]);
+        r.i[c] = T(r64.i[c]);
+        z.r[c] = z.i[c] = T(0);
+    }
+    FieldIO<PR>::store(S->slot[SL_Y], vh, i, z);
+    const Vec3<T> rs = FieldIO<PR>::store(S->slot[SL_R], vh, i, r);
+    Vec3<TD> o;
+    if (beta != 0.0) {
+        const auto d = FieldIO<PD>::load(S->slot[SL_D], vh, i);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            o.r[c] = TD(rs.r[c] + T(beta) * T(d.r[c]));
+            o.i[c] = TD(rs.i[c] + T(beta) * T(d.i[c]));
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            o.r[c] = TD(rs.r[c]);
+            o.i[c] = TD(rs.i[c]);
+        }
+    }
+    FieldIO<PD>::store(S->slot[SL_D], vh, i, o);
+}
+
+// x64 += y (the Sec. 3.2 update: x_{k+1} = x_k + y in FP64)
+template <int PR>
+__global__ void __launch_bounds__(kBlock) k_slab_accumulate(const VecArgs a)
 {
     const SlabDev *S = a.sl + blockIdx.y;
-    const int vh = a.g.Vh;
+    const int vh = a.vh;
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= vh) return;
+    Vec3<double> x = FieldIO<P64>::load(S->slot[SL_X64], vh, i);
+    const auto y = FieldIO<PR>::load(S->slot[SL_Y], vh, i);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        x.r[c] += double(y.r[c]);
+        x.i[c] += double(y.i[c]);
+    }
+    FieldIO<P64>::store(S->slot[SL_X64], vh, i, x);
+}
+
+// |slot|^2 partials of an FP64 slot
+__global__ void __launch_bounds__(kBlock) k_slab_norm(const VecArgs a, int slot)
+{
+    const SlabDev *S = a.sl + blockIdx.y;
+    const int vh = a.vh;
     const int i = blockIdx.x * kBlock + threadIdx.x;
     double n = 0.0;
     if (i < vh) {
-        const Vec3<double> v = FieldIO<P64>::load(S->slot[a.in], vh, i);
-        if (a.out >= 0) FieldIO<P64>::store(S->slot[a.out], vh, i, v);
+        const Vec3<double> v = FieldIO<P64>::load(S->slot[slot], vh, i);
 #pragma unroll
         for (int c = 0; c < 3; ++c) n += v.r[c] * v.r[c] + v.i[c] * v.i[c];
     }
@@ -361,7 +448,8 @@ enum SumUse { SUM_OUT = 0, SUM_ALPHA = 1, SUM_BETA = 2 };
 
 // One block: each slab's n partials in a fixed order, then the slab totals
 // in slab order.  SUM_ALPHA: alpha = delta / d^dag A d (set_alpha);
-// SUM_BETA: the update's |r|^2, beta and the stop tests of Fig. 1;
+// SUM_BETA: the update's |r|^2, beta, the stop tests of Fig. 1 and the
+// reliable-update trigger of Sec. 3.2 (|r|^2 < delta^2 max |r|^2);
 // SUM_OUT: *out = total.
 __global__ void __launch_bounds__(kBlock) k_slab_sum(const double *partials, int pstride, int n, int nslabs,
                                                      int use, CGState *st, double *out)
@@ -388,7 +476,9 @@ __global__ void __launch_bounds__(kBlock) k_slab_sum(const double *partials, int
         st->iter += 1;
         if (!isfinite(total)) st->flag = FLAG_BREAKDOWN;
         else if (total <= st->stop_r2) st->flag = FLAG_CONVERGED;
+        else if (st->trig2 > 0.0 && total < st->trig2 * st->rmax2) st->flag = FLAG_UPDATE;
         else if (st->iter >= st->iter_limit) st->flag = FLAG_MAXITER;
+        if (st->track_max && total > st->rmax2) st->rmax2 = total;
     }
 }
 
@@ -416,13 +506,15 @@ struct stg_slabs {
     int dims[4] = {0, 0, 0, 0};
     int P = 0, prec = 0, recon = 18;
     Geom g;                          // local lattice (Lx, Ly, Lz, Lt / P)
-    std::vector<LinkField> links;    // [P]
+    std::vector<LinkField> links;    // [P], in prec / recon
+    std::vector<LinkField> links64;  // [P], FP64 / 18-real, when prec is not FP64
     char *ghost = nullptr;           // [P][2 output parities] ghost t-links
     size_t ghost_bytes = 0;
-    char *fields = nullptr;          // [P][kSlabSlots]
+    char *ghost64 = nullptr;         // the same for links64
+    size_t ghost64_bytes = 0;
+    char *fields = nullptr;          // [P][kSlabSlots], 48 bytes per site each
     size_t field_bytes = 0;
-    char *faces = nullptr;           // [P][send 0, send 1, recv 0, recv 1]
-    size_t face_bytes = 0;           // bytes moved per face
+    char *faces = nullptr;           // [P][send 0, send 1, recv 0, recv 1], 48 bytes per face site
     size_t face_stride = 0;
     double *partials = nullptr;      // [P][pstride]
     int pstride = 0, nb_int = 0, nb_bnd = 0, nb_site = 0;
@@ -449,7 +541,10 @@ static void sl_free(stg_slabs *h)
     if (h->graph) cudaGraphExecDestroy(h->graph);
     for (LinkField &lf : h->links)
         if (lf.base) cudaFree(lf.base);
+    for (LinkField &lf : h->links64)
+        if (lf.base) cudaFree(lf.base);
     cudaFree(h->ghost);
+    cudaFree(h->ghost64);
     cudaFree(h->fields);
     cudaFree(h->faces);
     cudaFree(h->partials);
@@ -479,7 +574,7 @@ static stg_status sl_alloc(void **p, size_t n)
 struct SlabShape {
     Geom g;
     int st, nb_int, nb_bnd, nb_site, pstride;
-    size_t link_blk, ghost_bytes, field_bytes, face_bytes, face_stride;
+    size_t link_blk, ghost_bytes, link64_blk, ghost64_bytes, field_bytes, face_stride;
 };
 
 static SlabShape slab_shape(const int dims[4], int P, int prec, int recon)
@@ -495,9 +590,10 @@ static SlabShape slab_shape(const int dims[4], int P, int prec, int recon)
     s.pstride = s.nb_int + s.nb_bnd > s.nb_site ? s.nb_int + s.nb_bnd : s.nb_site;
     s.link_blk = sl_align((size_t)s.g.Vh * link_bytes(prec, recon));
     s.ghost_bytes = sl_align((size_t)s.st * link_bytes(prec, recon));
-    s.field_bytes = sl_align((size_t)s.g.Vh * field_site_bytes(prec));
-    s.face_bytes = (size_t)s.st * field_site_bytes(prec);
-    s.face_stride = sl_align(s.face_bytes);
+    s.link64_blk = prec == P64 ? 0 : sl_align((size_t)s.g.Vh * link_bytes(P64, 18));
+    s.ghost64_bytes = prec == P64 ? 0 : sl_align((size_t)s.st * link_bytes(P64, 18));
+    s.field_bytes = sl_align((size_t)s.g.Vh * 48);
+    s.face_stride = sl_align((size_t)s.st * 48);
     return s;
 }
 
@@ -506,6 +602,7 @@ static size_t slabs_bytes(const int dims[4], int P, int prec, int recon)
     const SlabShape s = slab_shape(dims, P, prec, recon);
     size_t n = (size_t)P * 8 * s.link_blk;                  // links
     n += (size_t)P * 2 * s.ghost_bytes;                      // ghost t-links
+    n += (size_t)P * (8 * s.link64_blk + 2 * s.ghost64_bytes);  // FP64 links of the CG's residual
     n += (size_t)P * kSlabSlots * s.field_bytes;             // fields
     n += (size_t)P * 4 * s.face_stride;                      // faces
     n += sl_align((size_t)P * s.pstride * sizeof(double));   // partials
@@ -516,7 +613,7 @@ static size_t slabs_bytes(const int dims[4], int P, int prec, int recon)
 // ---------------------------------------------------------------------------
 // one Dirac operation: collect, exchange, the slabs' Dslash
 // ---------------------------------------------------------------------------
-static stg_status sl_collect(stg_slabs *h, int slot, int direct, cudaStream_t s)
+static stg_status sl_collect(stg_slabs *h, int slot, int prec, int direct, cudaStream_t s)
 {
     CollectArgs c;
     c.sl = h->dev;
@@ -524,8 +621,8 @@ static stg_status sl_collect(stg_slabs *h, int slot, int direct, cudaStream_t s)
     c.vh = h->g.Vh;
     c.st = h->g.st;
     c.lts = h->g.L[3];
-    c.np = field_planes(h->prec, c.e);
-    c.words = (int)(h->face_bytes / 8);
+    c.np = field_planes(prec, c.e);
+    c.words = (int)((size_t)h->g.st * field_site_bytes(prec) / 8);
     c.direct = direct;
     const dim3 grid((unsigned)((2L * c.words + kBlock - 1) / kBlock), (unsigned)h->P);
     k_slab_collect<<<grid, kBlock, 0, s>>>(c);
@@ -535,22 +632,25 @@ static stg_status sl_collect(stg_slabs *h, int slot, int direct, cudaStream_t s)
 
 // COPY mode: slab r's slice 0 -> previous slab's forward ghost, its slice
 // Lts - 1 -> next slab's backward ghost (one copy per face and neighbour)
-static stg_status sl_exchange(stg_slabs *h, cudaStream_t s)
+static stg_status sl_exchange(stg_slabs *h, int prec, cudaStream_t s)
 {
+    const size_t bytes = (size_t)h->g.st * field_site_bytes(prec);
     for (int r = 0; r < h->P; ++r) {
-        STG_CUDA(cudaMemcpyAsync(h->face(h->prev(r), 2), h->face(r, 0), h->face_bytes, cudaMemcpyDeviceToDevice, s));
-        STG_CUDA(cudaMemcpyAsync(h->face(h->next(r), 3), h->face(r, 1), h->face_bytes, cudaMemcpyDeviceToDevice, s));
+        STG_CUDA(cudaMemcpyAsync(h->face(h->prev(r), 2), h->face(r, 0), bytes, cudaMemcpyDeviceToDevice, s));
+        STG_CUDA(cudaMemcpyAsync(h->face(h->next(r), 3), h->face(r, 1), bytes, cudaMemcpyDeviceToDevice, s));
     }
     return STG_OK;
 }
 
-static stg_status sl_halo(stg_slabs *h, int slot, cudaStream_t s)
+static stg_status sl_halo(stg_slabs *h, int slot, int prec, cudaStream_t s)
 {
-    STG_TRY(sl_collect(h, slot, h->mode == STG_SLAB_DIRECT, s));
-    if (h->mode == STG_SLAB_COPY) STG_TRY(sl_exchange(h, s));
+    STG_TRY(sl_collect(h, slot, prec, h->mode == STG_SLAB_DIRECT, s));
+    if (h->mode == STG_SLAB_COPY) STG_TRY(sl_exchange(h, prec, s));
     return STG_OK;
 }
 
+// EPI_NONE / EPI_A_DOT for every precision; the CG's epilogues for the
+// precisions it runs in (FP64, FP32, FX16)
 template <int P, int R>
 static void sl_launch_pr(int epi, dim3 grid, cudaStream_t s, const SlabArgs &a)
 {
@@ -558,16 +658,19 @@ static void sl_launch_pr(int epi, dim3 grid, cudaStream_t s, const SlabArgs &a)
     case EPI_NONE: k_slab_dslash<P, R, EPI_NONE><<<grid, kBlock, 0, s>>>(a); break;
     case EPI_A_DOT: k_slab_dslash<P, R, EPI_A_DOT><<<grid, kBlock, 0, s>>>(a); break;
     default:
-        if constexpr (P == P64) {
+        if constexpr (P == P64 || P == P32 || P == PX16) {
             if (epi == EPI_GATE) k_slab_dslash<P, R, EPI_GATE><<<grid, kBlock, 0, s>>>(a);
             else if (epi == EPI_A_CG) k_slab_dslash<P, R, EPI_A_CG><<<grid, kBlock, 0, s>>>(a);
-            else if (epi == EPI_RES) k_slab_dslash<P, R, EPI_RES><<<grid, kBlock, 0, s>>>(a);
+        }
+        if constexpr (P == P64) {
+            if (epi == EPI_RES) k_slab_dslash<P, R, EPI_RES><<<grid, kBlock, 0, s>>>(a);
         }
         break;
     }
 }
 
-// part 0: interior slices (none when Lts = 2); part 1: slices 0 and Lts - 1
+// part 0: interior slices (none when Lts = 2); part 1: slices 0 and Lts - 1;
+// part 2: both in one launch
 static stg_status sl_part(stg_slabs *h, int epi, SlabArgs a, int part, cudaStream_t s)
 {
     const int nb = part == 2 ? h->nb_int + h->nb_bnd : (part ? h->nb_bnd : h->nb_int);
@@ -576,8 +679,8 @@ static stg_status sl_part(stg_slabs *h, int epi, SlabArgs a, int part, cudaStrea
     a.pbase = part == 1 ? h->nb_int : 0;
     a.nb_int = h->nb_int;
     const dim3 grid((unsigned)nb, (unsigned)h->P);
-    const bool r12 = h->recon == 12;
-    switch (h->prec) {
+    const bool r12 = a.recon == 12;
+    switch (a.prec) {
     case P64: if (r12) sl_launch_pr<P64, 12>(epi, grid, s, a); else sl_launch_pr<P64, 18>(epi, grid, s, a); break;
     case P32: if (r12) sl_launch_pr<P32, 12>(epi, grid, s, a); else sl_launch_pr<P32, 18>(epi, grid, s, a); break;
     case P16: if (r12) sl_launch_pr<P16, 12>(epi, grid, s, a); else sl_launch_pr<P16, 18>(epi, grid, s, a); break;
@@ -605,6 +708,22 @@ static SlabArgs sl_args(const stg_slabs *h, int parity, int in, int out, int w, 
     a.pbase = 0;
     a.part = 0;
     a.nb_int = h->nb_int;
+    a.prec = h->prec;
+    a.recon = h->recon;
+    a.hi = 0;
+    return a;
+}
+
+// the same on the FP64 links (the FP64 / 18-real copy when the handle's
+// links are in another precision)
+static SlabArgs sl_args64(const stg_slabs *h, int parity, int in, int out, int w, int v, double m2)
+{
+    SlabArgs a = sl_args(h, parity, in, out, w, v, m2);
+    a.prec = P64;
+    if (h->prec != P64) {
+        a.recon = 18;
+        a.hi = 1;
+    }
     return a;
 }
 
@@ -613,13 +732,13 @@ static stg_status sl_dirac(stg_slabs *h, int epi, const SlabArgs &a, cudaStream_
     if (h->overlap) {
         STG_CUDA(cudaEventRecord(h->ev_fork, s));
         STG_CUDA(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
-        STG_TRY(sl_halo(h, a.in, h->side));
+        STG_TRY(sl_halo(h, a.in, a.prec, h->side));
         STG_CUDA(cudaEventRecord(h->ev_join, h->side));
         STG_TRY(sl_part(h, epi, a, 0, s));
         STG_CUDA(cudaStreamWaitEvent(s, h->ev_join, 0));
         return sl_part(h, epi, a, 1, s);
     }
-    STG_TRY(sl_halo(h, a.in, s));
+    STG_TRY(sl_halo(h, a.in, a.prec, s));
     return sl_part(h, epi, a, 2, s);
 }
 
@@ -648,21 +767,42 @@ static stg_status sl_write_state(stg_slabs *h, cudaStream_t s)
 namespace stg {
 
 // ---------------------------------------------------------------------------
-// CG of Fig. 1 on the decomposed operator (FP64)
+// CG on the decomposed operator: Fig. 1 in FP64 for FP64 handles; for FP32 /
+// FX16 handles, inner iterations in that precision with the reliable
+// updates of Sec. 3.2 (x += y and r = b - A x with the FP64 links) and the
+// restart of Eq. 6
 // ---------------------------------------------------------------------------
-// one iteration: t = D_oe d; q = m^2 d - D_eo t, d^dag q -> alpha; x, r
-// update with |r|^2 -> beta and the stop tests; d = r + beta d
+static VecArgs sl_vec(const stg_slabs *h)
+{
+    VecArgs v;
+    v.sl = h->dev;
+    v.vh = h->g.Vh;
+    v.state = h->state;
+    v.partials = h->partials;
+    v.pstride = h->pstride;
+    return v;
+}
+
+#define SL_DISPATCH_PD(pd, KERNEL, ...)                                                          \
+    do {                                                                                         \
+        if ((pd) == P64) KERNEL<P64, P64><<<grid, kBlock, 0, s>>>(__VA_ARGS__);                  \
+        else if ((pd) == P32) KERNEL<P32, P32><<<grid, kBlock, 0, s>>>(__VA_ARGS__);             \
+        else KERNEL<PX16, P32><<<grid, kBlock, 0, s>>>(__VA_ARGS__);                             \
+    } while (0)
+
+// one inner iteration: t = D_oe d; q = m^2 d - D_eo t, d^dag q -> alpha;
+// y, r update with |r|^2 -> beta and the stop / update tests; d = r + beta d
 static stg_status sl_iteration(stg_slabs *h, cudaStream_t s)
 {
     STG_TRY(sl_dirac(h, EPI_GATE, sl_args(h, 1, SL_D, SL_T, -1, -1, 0.0), s));
     STG_TRY(sl_dirac(h, EPI_A_CG, sl_args(h, 0, SL_T, SL_Q, SL_D, -1, 0.0), s));
     STG_TRY(sl_sum(h, h->nb_int + h->nb_bnd, SUM_ALPHA, nullptr, s));
-    const SlabArgs av = sl_args(h, 0, -1, -1, -1, -1, 0.0);
+    const VecArgs v = sl_vec(h);
     const dim3 grid((unsigned)h->nb_site, (unsigned)h->P);
-    k_slab_update<<<grid, kBlock, 0, s>>>(av);
+    SL_DISPATCH_PD(h->prec, k_slab_update, v);
     STG_CUDA(cudaGetLastError());
     STG_TRY(sl_sum(h, h->nb_site, SUM_BETA, nullptr, s));
-    k_slab_xpay<<<grid, kBlock, 0, s>>>(av);
+    SL_DISPATCH_PD(h->prec, k_slab_xpay, v);
     STG_CUDA(cudaGetLastError());
     return STG_OK;
 }
@@ -711,22 +851,21 @@ static stg_status sl_graph(stg_slabs *h, int iters)
     return STG_OK;
 }
 
-// r = b - A x (slot R) and |r|^2 into state->result
+// r64 = b - A x64 with the FP64 links, |r64|^2 into state->result
 static stg_status sl_true_residual(stg_slabs *h, double m2, cudaStream_t s, double *rr)
 {
-    STG_TRY(sl_dirac(h, EPI_NONE, sl_args(h, 1, SL_X, SL_T, -1, -1, 0.0), s));
-    STG_TRY(sl_dirac(h, EPI_RES, sl_args(h, 0, SL_T, SL_R, SL_B, SL_X, m2), s));
+    STG_TRY(sl_dirac(h, EPI_NONE, sl_args64(h, 1, SL_X64, SL_T64, -1, -1, 0.0), s));
+    STG_TRY(sl_dirac(h, EPI_RES, sl_args64(h, 0, SL_T64, SL_R64, SL_B64, SL_X64, m2), s));
     STG_TRY(sl_sum(h, h->nb_int + h->nb_bnd, SUM_OUT, &h->state->result, s));
     STG_TRY(sl_read_state(h, s));
     *rr = h->state_host->result;
     return STG_OK;
 }
 
-// slot out = slot in (out < 0: none) and |in|^2 into state->result
-static stg_status sl_copy_norm(stg_slabs *h, int in, int out, cudaStream_t s, double *nn)
+static stg_status sl_norm64(stg_slabs *h, int slot, cudaStream_t s, double *nn)
 {
     const dim3 grid((unsigned)h->nb_site, (unsigned)h->P);
-    k_slab_copy_norm<<<grid, kBlock, 0, s>>>(sl_args(h, 0, in, out, -1, -1, 0.0));
+    k_slab_norm<<<grid, kBlock, 0, s>>>(sl_vec(h), slot);
     STG_CUDA(cudaGetLastError());
     STG_TRY(sl_sum(h, h->nb_site, SUM_OUT, &h->state->result, s));
     STG_TRY(sl_read_state(h, s));
@@ -734,34 +873,37 @@ static stg_status sl_copy_norm(stg_slabs *h, int in, int out, cudaStream_t s, do
     return STG_OK;
 }
 
-static stg_status sl_load(stg_slabs *h, int slot, const double *canon, cudaStream_t s)
+static stg_status sl_load(stg_slabs *h, int slot, int prec, const double *canon, cudaStream_t s)
 {
     for (int r = 0; r < h->P; ++r)
-        STG_TRY(pack_field(h->g, h->prec, canon + (size_t)r * h->g.Vh * 6, h->field(r, slot), s));
+        STG_TRY(pack_field(h->g, prec, canon + (size_t)r * h->g.Vh * 6, h->field(r, slot), s));
     return STG_OK;
 }
 
-static stg_status sl_store(stg_slabs *h, int slot, double *canon, cudaStream_t s)
+static stg_status sl_store(stg_slabs *h, int slot, int prec, double *canon, cudaStream_t s)
 {
     for (int r = 0; r < h->P; ++r)
-        STG_TRY(unpack_field(h->g, h->prec, h->field(r, slot), canon + (size_t)r * h->g.Vh * 6, s));
+        STG_TRY(unpack_field(h->g, prec, h->field(r, slot), canon + (size_t)r * h->g.Vh * 6, s));
     return STG_OK;
 }
 
 static stg_status sl_cg(stg_slabs *h, const double *src, double *x, double mass, double tol, long maxiter,
-                        stg_cg_stats *stats, cudaStream_t s)
+                        double delta, stg_cg_stats *stats, cudaStream_t s)
 {
     timespec t0, t1;
     clock_gettime(CLOCK_MONOTONIC, &t0);
     stg_cg_stats st = {};
+    const bool plain = h->prec == P64;
+    const int pr = slab_pr(h->prec);
     const double m2 = mass * mass;
     const long vh_total = (long)h->g.Vh * h->P;
     if (maxiter <= 0) maxiter = 10L * 3L * vh_total;
     const int chunk = vh_total >= (1L << 19) ? 16 : 32;
-    STG_TRY(sl_load(h, SL_B, src, s));
-    STG_TRY(sl_load(h, SL_X, x, s));
+    const dim3 grid((unsigned)h->nb_site, (unsigned)h->P);
+    STG_TRY(sl_load(h, SL_B64, P64, src, s));
+    STG_TRY(sl_load(h, SL_X64, P64, x, s));
     double bb = 0.0, rr = 0.0;
-    STG_TRY(sl_copy_norm(h, SL_B, -1, s, &bb));
+    STG_TRY(sl_norm64(h, SL_B64, s, &bb));
     if (!isfinite(bb)) {
         set_error("stg_slabs_cg_solve: the source has non-finite entries");
         return STG_ERR_INVALID_ARG;
@@ -783,16 +925,18 @@ static stg_status sl_cg(stg_slabs *h, const double *src, double *x, double mass,
     CGState *hs = h->state_host;
     int breakdowns = 0;
     long long iters = 0;
+    double beta = 0.0;
     while (status == STG_OK && rr > stop) {
-        // (re)start: d = r
-        double dummy;
-        status = sl_copy_norm(h, SL_R, SL_D, s, &dummy);
-        if (status != STG_OK) break;
-        launches += 2;
+        // (re)start: y = 0, r = r64, d = r + beta d (Fig. 2; Eq. 6)
+        SL_DISPATCH_PD(h->prec, k_slab_reset, sl_vec(h), beta);
+        STG_CUDA(cudaGetLastError());
+        launches += 1;
         hs->delta_new = rr;
         hs->delta_old = rr;
+        hs->rmax2 = rr;
         hs->stop_r2 = stop;
-        hs->trig2 = 0.0;
+        hs->trig2 = plain ? 0.0 : delta * delta;
+        hs->track_max = plain ? 0 : 1;
         hs->m2 = m2;
         hs->iter = iters;
         hs->iter_limit = maxiter;
@@ -812,10 +956,15 @@ static stg_status sl_cg(stg_slabs *h, const double *src, double *x, double mass,
         }
         if (status != STG_OK) break;
         const int flag = hs->flag;
+        const double delta_old = hs->delta_old;
         iters = hs->iter;
         st.iter_res = sqrt(hs->delta_new / bb);
+        // x_{k+1} = x_k + y, r_{k+1} = b - A x_{k+1} (Sec. 3.2)
+        if (pr == P64) k_slab_accumulate<P64><<<grid, kBlock, 0, s>>>(sl_vec(h));
+        else k_slab_accumulate<P32><<<grid, kBlock, 0, s>>>(sl_vec(h));
+        STG_CUDA(cudaGetLastError());
         status = sl_true_residual(h, m2, s, &rr);
-        launches += 2 * 3 + 1;
+        launches += 1 + 2 * 3 + 1;
         st.updates += 1;
         if (status != STG_OK || rr <= stop) break;
         if (!isfinite(rr)) {
@@ -828,20 +977,26 @@ static stg_status sl_cg(stg_slabs *h, const double *src, double *x, double mass,
             status = STG_ERR_NOT_CONVERGED;
             break;
         }
-        if (flag == FLAG_BREAKDOWN && ++breakdowns > 3) {
-            set_error("stg_slabs_cg_solve: d^dag A d <= 0 or non-finite reduction");
-            status = STG_ERR_BREAKDOWN;
-            break;
+        beta = 0.0;
+        if (flag == FLAG_BREAKDOWN) {
+            if (++breakdowns > 3) {
+                set_error("stg_slabs_cg_solve: d^dag A d <= 0 or non-finite reduction");
+                status = STG_ERR_BREAKDOWN;
+                break;
+            }
+        } else if (!plain) {
+            beta = rr / delta_old;  // Eq. 6: d^y_0 = r + beta d, d kept
         }
     }
     if (status == STG_OK || status == STG_ERR_NOT_CONVERGED) {
-        stg_status u = sl_store(h, SL_X, x, s);
+        stg_status u = sl_store(h, SL_X64, P64, x, s);
         cudaError_t e = cudaStreamSynchronize(s);
         if (u != STG_OK) status = u;
         else if (e != cudaSuccess) status = cuda_fail(e, "cudaStreamSynchronize");
         launches += h->P;
     }
     st.iters = (long)iters;
+    st.sloppy_iters = plain ? 0 : (long)iters;
     st.true_res = sqrt(rr / bb);
     if (st.updates == 0) st.iter_res = st.true_res;
     st.launches = launches;
@@ -866,9 +1021,9 @@ static stg_status sl_profile(stg_slabs *h, int reps, double ms[4], cudaStream_t 
             if (round) STG_CUDA(cudaEventRecord(h->ev_t[0], s));
             for (int k = 0; k < n; ++k) {
                 if (phase == 0) {
-                    STG_TRY(sl_collect(h, a.in, h->mode == STG_SLAB_DIRECT, s));
+                    STG_TRY(sl_collect(h, a.in, h->prec, h->mode == STG_SLAB_DIRECT, s));
                 } else if (phase == 1) {
-                    if (h->mode == STG_SLAB_COPY) STG_TRY(sl_exchange(h, s));
+                    if (h->mode == STG_SLAB_COPY) STG_TRY(sl_exchange(h, h->prec, s));
                 } else if (phase == 2) {
                     STG_TRY(sl_part(h, EPI_NONE, a, 2, s));
                 } else {
@@ -939,14 +1094,15 @@ stg_status stg_slabs_create(const int dims[4], const double *links_host, int nsl
     const SlabShape sh = slab_shape(dims, nslabs, prec, recon);
     h->g = sh.g;
     h->ghost_bytes = sh.ghost_bytes;
+    h->ghost64_bytes = sh.ghost64_bytes;
     h->field_bytes = sh.field_bytes;
-    h->face_bytes = sh.face_bytes;
     h->face_stride = sh.face_stride;
     h->nb_int = sh.nb_int;
     h->nb_bnd = sh.nb_bnd;
     h->nb_site = sh.nb_site;
     h->pstride = sh.pstride;
     h->links.resize(nslabs);
+    if (prec != STG_FP64) h->links64.resize(nslabs);
     const int P = nslabs, lts = h->g.L[3], st_ = h->g.st;
     const size_t vh = (size_t)h->g.Vh;
 
@@ -958,7 +1114,9 @@ stg_status stg_slabs_create(const int dims[4], const double *links_host, int nsl
         cudaError_t e = cudaMemcpyAsync(ucan, links_host + (size_t)r * (canon_bytes / sizeof(double)), canon_bytes,
                                         cudaMemcpyHostToDevice, s);
         if (e != cudaSuccess) st = cuda_fail(e, "cudaMemcpyAsync(links)");
-        if (st == STG_OK) st = pack_links_flip(h->g, ucan, prec, recon, r == P - 1 ? lts - 1 : -1, &h->links[r], s);
+        const int t_flip = r == P - 1 ? lts - 1 : -1;
+        if (st == STG_OK) st = pack_links_flip(h->g, ucan, prec, recon, t_flip, &h->links[r], s);
+        if (st == STG_OK && prec != STG_FP64) st = pack_links_flip(h->g, ucan, P64, 18, t_flip, &h->links64[r], s);
         if (st == STG_OK) {
             e = cudaStreamSynchronize(s);  // the staging buffer is reused
             if (e != cudaSuccess) st = cuda_fail(e, "cudaStreamSynchronize");
@@ -966,6 +1124,7 @@ stg_status stg_slabs_create(const int dims[4], const double *links_host, int nsl
     }
     cudaFree(ucan);
     if (st == STG_OK) st = sl_alloc((void **)&h->ghost, (size_t)P * 2 * h->ghost_bytes);
+    if (st == STG_OK && prec != STG_FP64) st = sl_alloc((void **)&h->ghost64, (size_t)P * 2 * h->ghost64_bytes);
     if (st == STG_OK) st = sl_alloc((void **)&h->fields, (size_t)P * kSlabSlots * h->field_bytes);
     if (st == STG_OK) st = sl_alloc((void **)&h->faces, (size_t)P * 4 * h->face_stride);
     if (st == STG_OK) st = sl_alloc((void **)&h->partials, (size_t)P * h->pstride * sizeof(double));
@@ -982,21 +1141,26 @@ stg_status stg_slabs_create(const int dims[4], const double *links_host, int nsl
         if (e != cudaSuccess) st = cuda_fail(e, "stg_slabs_create");
     }
     // ghost t-links: for output parity p, the previous slab's block (1 - p, t)
-    // at its last slice, plane by plane (planes of stride st)
-    int le[9];
-    const int nlp = link_planes(prec, recon, le);
-    for (int r = 0; r < P && st == STG_OK; ++r) {
-        for (int p = 0; p < 2 && st == STG_OK; ++p) {
-            const char *src = h->links[h->prev(r)].blk(1 - p, 3);
-            char *dst = h->ghost + ((size_t)r * 2 + p) * h->ghost_bytes;
-            size_t off_src = 0, off_dst = 0;
-            for (int k = 0; k < nlp && st == STG_OK; ++k) {
-                const size_t n = (size_t)st_ * le[k];
-                cudaError_t e = cudaMemcpyAsync(dst + off_dst, src + off_src + (size_t)(lts - 1) * n, n,
-                                                cudaMemcpyDeviceToDevice, s);
-                if (e != cudaSuccess) st = cuda_fail(e, "cudaMemcpyAsync(ghost links)");
-                off_src += vh * le[k];
-                off_dst += n;
+    // at its last slice, plane by plane (planes of stride st); for each link set
+    for (int set = 0; set < (prec != STG_FP64 ? 2 : 1); ++set) {
+        const std::vector<LinkField> &lk = set ? h->links64 : h->links;
+        char *ghost = set ? h->ghost64 : h->ghost;
+        const size_t gbytes = set ? h->ghost64_bytes : h->ghost_bytes;
+        int le[9];
+        const int nlp = set ? link_planes(P64, 18, le) : link_planes(prec, recon, le);
+        for (int r = 0; r < P && st == STG_OK; ++r) {
+            for (int p = 0; p < 2 && st == STG_OK; ++p) {
+                const char *src = lk[h->prev(r)].blk(1 - p, 3);
+                char *dst = ghost + ((size_t)r * 2 + p) * gbytes;
+                size_t off_src = 0, off_dst = 0;
+                for (int k = 0; k < nlp && st == STG_OK; ++k) {
+                    const size_t n = (size_t)st_ * le[k];
+                    cudaError_t e = cudaMemcpyAsync(dst + off_dst, src + off_src + (size_t)(lts - 1) * n, n,
+                                                    cudaMemcpyDeviceToDevice, s);
+                    if (e != cudaSuccess) st = cuda_fail(e, "cudaMemcpyAsync(ghost links)");
+                    off_src += vh * le[k];
+                    off_dst += n;
+                }
             }
         }
     }
@@ -1007,6 +1171,9 @@ stg_status stg_slabs_create(const int dims[4], const double *links_host, int nsl
             memset(&d, 0, sizeof(d));
             for (int k = 0; k < 8; ++k) d.lk[k] = h->links[r].blk(k / 4, k % 4);
             for (int p = 0; p < 2; ++p) d.ghost_lk[p] = h->ghost + ((size_t)r * 2 + p) * h->ghost_bytes;
+            for (int k = 0; k < 8; ++k) d.lk64[k] = prec != STG_FP64 ? h->links64[r].blk(k / 4, k % 4) : d.lk[k];
+            for (int p = 0; p < 2; ++p)
+                d.ghost64[p] = prec != STG_FP64 ? h->ghost64 + ((size_t)r * 2 + p) * h->ghost64_bytes : d.ghost_lk[p];
             for (int k = 0; k < kSlabSlots; ++k) d.slot[k] = h->field(r, k);
             d.send[0] = h->face(r, 0);
             d.send[1] = h->face(r, 1);
@@ -1052,28 +1219,28 @@ stg_status stg_slabs_set_exchange(stg_slabs *h, int mode, int overlap)
 
 stg_status stg_slabs_load(stg_slabs *h, int slot, const double *canon_dev, stg_stream_t stream)
 {
-    if (!h || !canon_dev || slot < 0 || slot >= kSlabSlots) {
+    if (!h || !canon_dev || slot < 0 || slot >= kUserSlots) {
         set_error("stg_slabs_load: NULL argument or slot outside 0..5");
         return STG_ERR_INVALID_ARG;
     }
     SlScope ds(h->device);
-    return sl_load(h, slot, canon_dev, (cudaStream_t)stream);
+    return sl_load(h, slot, h->prec, canon_dev, (cudaStream_t)stream);
 }
 
 stg_status stg_slabs_store(stg_slabs *h, int slot, double *canon_dev, stg_stream_t stream)
 {
-    if (!h || !canon_dev || slot < 0 || slot >= kSlabSlots) {
+    if (!h || !canon_dev || slot < 0 || slot >= kUserSlots) {
         set_error("stg_slabs_store: NULL argument or slot outside 0..5");
         return STG_ERR_INVALID_ARG;
     }
     SlScope ds(h->device);
-    return sl_store(h, slot, canon_dev, (cudaStream_t)stream);
+    return sl_store(h, slot, h->prec, canon_dev, (cudaStream_t)stream);
 }
 
 stg_status stg_slabs_dslash(stg_slabs *h, int out_parity, int in_slot, int out_slot, stg_stream_t stream)
 {
-    if (!h || (out_parity != 0 && out_parity != 1) || in_slot < 0 || in_slot >= kSlabSlots || out_slot < 0 ||
-        out_slot >= kSlabSlots || in_slot == out_slot) {
+    if (!h || (out_parity != 0 && out_parity != 1) || in_slot < 0 || in_slot >= kUserSlots || out_slot < 0 ||
+        out_slot >= kUserSlots || in_slot == out_slot) {
         set_error("stg_slabs_dslash: NULL handle, parity not 0 / 1, or slots outside 0..5 or equal");
         return STG_ERR_INVALID_ARG;
     }
@@ -1084,7 +1251,7 @@ stg_status stg_slabs_dslash(stg_slabs *h, int out_parity, int in_slot, int out_s
 stg_status stg_slabs_apply_A_dot(stg_slabs *h, double mass, int in_slot, int out_slot, double *dot_dev,
                                  stg_stream_t stream)
 {
-    if (!h || !dot_dev || in_slot < 0 || in_slot >= kSlabSlots || out_slot < 0 || out_slot >= kSlabSlots ||
+    if (!h || !dot_dev || in_slot < 0 || in_slot >= kUserSlots || out_slot < 0 || out_slot >= kUserSlots ||
         in_slot == out_slot || in_slot == SL_T || out_slot == SL_T || !isfinite(mass)) {
         set_error("stg_slabs_apply_A_dot: NULL argument, non-finite mass, or slots outside 0..5, equal, "
                   "or slot 4 (the odd intermediate)");
@@ -1109,12 +1276,14 @@ stg_status stg_slabs_cg_solve(stg_slabs *h, const double *src_dev, double *x_dev
         set_error("stg_slabs_cg_solve: mass must be finite and >= 0, tol finite and > 0, maxiter >= 0");
         return STG_ERR_INVALID_ARG;
     }
-    if (h->prec != STG_FP64) {
-        set_error("stg_slabs_cg_solve: the decomposed CG runs in FP64 (create the slabs with STG_FP64)");
+    if (h->prec != STG_FP64 && h->prec != STG_FP32 && h->prec != STG_FX16) {
+        set_error("stg_slabs_cg_solve: the decomposed CG runs with FP64, FP32 or FX16 slabs");
         return STG_ERR_UNSUPPORTED;
     }
+    // the reliable-update threshold of stg_cg_params_default for the precision
+    const double delta = h->prec == STG_FP32 ? 0.05 : 0.25;
     SlScope ds(h->device);
-    return sl_cg(h, src_dev, x_dev, mass, tol, maxiter, stats, (cudaStream_t)stream);
+    return sl_cg(h, src_dev, x_dev, mass, tol, maxiter, delta, stats, (cudaStream_t)stream);
 }
 
 stg_status stg_slabs_profile(stg_slabs *h, int reps, double ms[4], stg_stream_t stream)

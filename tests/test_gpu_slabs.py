@@ -10,8 +10,9 @@
 - COPY, DIRECT and the overlapped schedule give bitwise the same output and
   the same d^dag A d.
 - apply_A_dot against the oracle's A and its inner product.
-- The FP64 CG on the slabs: true residual with the oracle's A <= tol, and the
-  solution within kappa_hat tol of the oracle's.
+- The CG on the slabs (FP64; FP32 and FX16 inner iterations with reliable
+  updates): true residual with the oracle's A <= tol, and the solution
+  within kappa_hat tol of the oracle's.
 """
 import numpy as np
 import pytest
@@ -173,12 +174,34 @@ def test_slab_cg_matches_oracle(dims, P, mode):
     assert stats["true_res"] <= tol
 
 
+@pytest.mark.parametrize("prec,recon,P", [(stg.STG_FP32, 12, 2), (stg.STG_FX16, 12, 3),
+                                          (stg.STG_FP32, 18, 1)])
+def test_slab_mixed_cg_matches_oracle(prec, recon, P):
+    """Inner iterations in FP32 / FX16 on the slabs, reliable updates with the
+    FP64 links (Sec. 3.2), to the FP64 true residual."""
+    dims, mass, tol = (6, 4, 10, 12), 0.05, 1e-10
+    U = gen.gauge_field(dims, "exp", seed=4, eps=0.5)
+    b = gen.source(dims, seed=8)
+    x_ref, info = oracle.cg(dims, U, mass, b, tol=tol)
+    with Slabs(dims, U, P, prec, recon, stg.STG_SLAB_DIRECT, 0) as s:
+        bd = _to_dev(b)
+        xd = torch.zeros_like(bd)
+        stats = stg.stg_slabs_cg_solve(s.h, bd, xd, mass, tol)
+        x = xd.cpu().numpy()
+    res = np.linalg.norm(b - oracle.apply_A(dims, U, mass, x)) / np.linalg.norm(b)
+    assert res <= tol * 1.01, stats
+    kappa = (mass ** 2 + 64.0) / mass ** 2
+    assert rel(x, x_ref) <= kappa * tol
+    assert stats["updates"] >= 2 and stats["sloppy_iters"] == stats["iters"]
+    assert stats["iters"] < 3 * info["iters"], (stats, info)
+
+
 def test_slab_cg_unsupported_precision_and_profile():
     dims = (4, 4, 4, 8)
     U = gen.gauge_field(dims, "haar", seed=0)
     b = _to_dev(gen.source(dims, seed=1))
     x = torch.zeros_like(b)
-    with Slabs(dims, U, 2, stg.STG_FP32, 12) as s:
+    with Slabs(dims, U, 2, stg.STG_FP16, 12) as s:
         with pytest.raises(stg.StgError) as e:
             stg.stg_slabs_cg_solve(s.h, b, x, 0.1, 1e-8)
         assert e.value.status == stg.STG_ERR_UNSUPPORTED
