@@ -854,7 +854,8 @@ def run_slabs(args):
     operation in each schedule), in FP64/18 and FP32/12, beside the
     undecomposed Dslash of the same lattice; then the CG of 16^3 x 32 (m =
     0.01, tol 1e-10) on 4 slabs against the undecomposed solver, in FP64 and
-    with FP32 / 12-real inner iterations and FP64 reliable updates."""
+    with FP32 / 12-real inner iterations and FP64 reliable updates, and the
+    32^3 x 64 solve of the default workload (FX16 / 12-real inner) on 4 slabs."""
     import torch
 
     import gen
@@ -937,6 +938,16 @@ def run_slabs(args):
         stg.stg_slabs_destroy(h)
     cg["mixed_f32_12_4_slabs_direct"] = {"seconds": st["seconds"], "iters": st["iters"],
                                          "updates": st["updates"], "true_res": st["true_res"]}
+    # the C3 solve (32^3 x 64, m = 0.005, FX16 / 12-real inner) on 4 slabs
+    h = stg.stg_slabs_create(dims, U, 4, stg.STG_FX16, 12)
+    try:
+        stg.stg_slabs_set_exchange(h, stg.STG_SLAB_DIRECT, 0)
+        x = torch.zeros_like(b)
+        st = stg.stg_slabs_cg_solve(h, b, x, 0.005, tol)
+    finally:
+        stg.stg_slabs_destroy(h)
+    cg["c3_fx16_12_4_slabs_direct"] = {"seconds": st["seconds"], "iters": st["iters"],
+                                       "updates": st["updates"], "true_res": st["true_res"]}
     print(json.dumps({
         "metric": METRIC, "workload": "slabs: t-slab decomposition of 32^3x64 on one GPU "
         "(Table 1 breakdown per Dirac operation); FP64 and mixed CG of 16^3x32 on 4 slabs",
