@@ -390,10 +390,12 @@ size_t stg_lgroup_bytes(int max_systems, long max_vh, stg_prec sloppy);
 stg_status stg_mrhs_tuning(const stg_gauge *g, stg_prec prec, int nrhs, int *rhs_block,
                            int *threads_per_site);
 
-/* Fill params with the defaults: RELIABLE, sloppy = handle's sloppy
- * precision, delta = 0.05 for FP32, 0.25 for FP16 / FX16 / BF16 inner iterations
- * (0.1 without a handle), maxiter = 0 (10 N_dim), check_every = 0 (auto),
- * timing = 0. */
+/* Fill params with the defaults: sloppy = handle's sloppy precision; RELIABLE
+ * with delta = 0.05 for FP32, 0.25 for FX16 / BF16 inner iterations (0.1
+ * without a handle); REFINE with delta = 0.02 for FP16 (its inner search
+ * direction is too inexact to carry across an update: measured on 32^3x64,
+ * m = 0.005, 2652 iterations against 8203 for RELIABLE at 0.25);
+ * maxiter = 0 (10 N_dim), check_every = 0 (auto), timing = 0. */
 stg_status stg_cg_params_default(const stg_gauge *g, stg_cg_params *params);
 
 /*

@@ -88,6 +88,33 @@ static stg_status check_field_prec(const stg_gauge *g, int prec, const LinkField
 
 using namespace stg;
 
+namespace stg {
+
+// Defaults for inner iterations in `sloppy` (see stg_cg_params_default).
+void cg_params_for(int sloppy, stg_cg_params *p)
+{
+    p->sloppy = sloppy;
+    // eps^in (Sec. 3.2 leaves it open): the lower the inner precision, the
+    // sooner the iterated residual drifts and the more often an update pays;
+    // measured on 32^3x64, m = 0.005 (FP32: 0.03-0.05 best, FX16 / BF16:
+    // 0.2-0.3).  IEEE FP16 (11 significand bits) is the exception: the Eq. 6
+    // start carries its inner search direction into the next cycle and costs
+    // it 8203 iterations at delta 0.25, while Fig. 2's restart from the true
+    // residual with inner solves to 0.02 takes 2652 (FX16 with Eq. 6: 2593)
+    if (sloppy == STG_FP16) {
+        p->policy = STG_CG_REFINE;
+        p->delta = 0.02;
+    } else {
+        p->policy = STG_CG_RELIABLE;
+        p->delta = (sloppy == STG_FP32) ? 0.05 : (sloppy == STG_FP64 ? 0.1 : 0.25);
+    }
+    p->maxiter = 0;
+    p->check_every = 0;
+    p->timing = 0;
+}
+
+}  // namespace stg
+
 extern "C" {
 
 int stg_version(void) { return 1; }
@@ -253,15 +280,7 @@ stg_status stg_cg_params_default(const stg_gauge *g, stg_cg_params *p)
         set_error("stg_cg_params_default: NULL params");
         return STG_ERR_INVALID_ARG;
     }
-    p->policy = STG_CG_RELIABLE;
-    p->sloppy = g ? g->sloppy : STG_FP64;
-    // eps^in (Sec. 3.2 leaves it open): the lower the inner precision, the
-    // sooner the iterated residual drifts and the more often an update pays;
-    // measured on 32^3x64, m = 0.005 (FP32: 0.03-0.05 best, 16-bit: 0.2-0.3)
-    p->delta = (p->sloppy == STG_FP32) ? 0.05 : (p->sloppy == STG_FP64 ? 0.1 : 0.25);
-    p->maxiter = 0;
-    p->check_every = 0;
-    p->timing = 0;
+    stg::cg_params_for(g ? g->sloppy : STG_FP64, p);
     return STG_OK;
 }
 

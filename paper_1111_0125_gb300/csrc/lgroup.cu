@@ -674,9 +674,7 @@ stg_status stg_lgroup_create(int max_systems, long max_vh, stg_prec sloppy, int 
     if (params) {
         p = *params;
     } else {
-        stg_cg_params_default(nullptr, &p);
-        p.sloppy = sloppy;
-        p.delta = (sloppy == STG_FP32) ? 0.05 : (sloppy == STG_FP64 ? 0.1 : 0.25);
+        cg_params_for(sloppy, &p);  // the defaults of stg_cg_params_default
     }
     if (p.policy < STG_CG_RELIABLE || p.policy > STG_CG_REFINE || !(p.delta > 0.0 && p.delta < 1.0) ||
         p.maxiter < 0 || p.check_every < 0) {

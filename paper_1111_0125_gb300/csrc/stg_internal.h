@@ -122,6 +122,9 @@ stg_status cuda_fail(cudaError_t e, const char *what);
 
 Geom make_geom(const int dims[4]);
 
+// stg_cg_params defaults for inner iterations in `sloppy` (api.cu)
+void cg_params_for(int sloppy, stg_cg_params *p);
+
 const LinkField *links_for(const stg_gauge *g, int prec);
 
 // Reduction scratch: partial sums (one double per block) and the state.
