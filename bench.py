@@ -69,6 +69,9 @@ def parse():
     ap.add_argument("--eps", type=float, default=0.6)
     ap.add_argument("--delta", type=float, default=None,
                     help="reliable-update threshold (default: the library's per-precision default)")
+    ap.add_argument("--policy", default=None, choices=["reliable", "refine"],
+                    help="update policy of the mixed CG (default: the library's per-precision "
+                         "default: refine for f16, reliable otherwise)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 CG comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -407,12 +410,22 @@ def run_reference(args, dims):
 METRIC = "Dslash GB/s vs HBM peak; CG time to 1e-10 residual mixed vs FP64; p99 latency"
 
 
+# the library's per-precision defaults (stg_cg_params_default), for the
+# config of a line that did not set them from a handle (the reference arm)
+DEFAULT_POLICY = {"f32": ("reliable", 0.05), "fx16": ("reliable", 0.25), "bf16": ("reliable", 0.25),
+                  "f16": ("refine", 0.02)}
+
+
 def config_dict(args, dims):
+    if args.policy is None or args.delta is None:
+        pol, dl = DEFAULT_POLICY[args.sloppy]
+        args.policy = args.policy if args.policy is not None else pol
+        args.delta = args.delta if args.delta is not None else dl
     return {"workload": workload_name(dims, args.tol), "lattice": "x".join(str(d) for d in dims),
             "mass": args.mass, "tol": args.tol, "links": f"exp(i*{args.eps}*H) SU(3), seed 0",
             "source": "complex Gaussian, seed 1+rank", "sloppy_storage": args.sloppy,
             "compute": "f32 inner iterations; f64 reliable updates and grid sums",
-            "recon": args.recon, "reliable_delta": args.delta, "policy": "reliable",
+            "recon": args.recon, "reliable_delta": args.delta, "policy": args.policy,
             "l2": "inputs larger than L2 (links alone exceed 129 MB); no flush",
             "parallelism": f"replicas{args.gpus}"}
 
@@ -1014,10 +1027,13 @@ def main():
             print(json.dumps({"kernels_only": True, "lattice": dims, "reps": args.reps}))
         return
 
-    params = g.params(policy=stg.STG_CG_RELIABLE, sloppy=sloppy, timing=1)
+    params = g.params(sloppy=sloppy, timing=1)
+    if args.policy is not None:
+        params.policy = {"reliable": stg.STG_CG_RELIABLE, "refine": stg.STG_CG_REFINE}[args.policy]
     if args.delta is not None:
         params.delta = args.delta
     args.delta = params.delta
+    args.policy = {stg.STG_CG_RELIABLE: "reliable", stg.STG_CG_REFINE: "refine"}[params.policy]
 
     def solve():
         x = torch.zeros_like(b)
