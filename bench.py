@@ -3,10 +3,12 @@
 
 One step = one complete mixed-precision CG solve A x = b to a true residual
 |b - A x| <= 1e-10 |b| on a 32^3 x 64 lattice (m = 0.005, exp(i 0.6 H) SU(3)
-links, complex Gaussian source), i.e. every kernel of the path: Dslash
-half-passes, the fused A operator with d^dag A d, the CG vector updates and
-the FP64 reliable updates.  Inputs are resident in HBM when the timed region
-starts; the working set (links 403 MB at FP32 / 12-real) is larger than L2.
+links, complex Gaussian source) with IEEE FP16 storage of links (12-real)
+and fields (per-site scale), FP32 arithmetic and FP64 updates, i.e. every
+kernel of the path: Dslash half-passes, the fused A operator with d^dag A d,
+the CG vector updates and the FP64 true-residual updates.  Inputs are
+resident in HBM when the timed region starts; the working set (links 201 MB
+at 16-bit / 12-real, plus their tile-major copy) is larger than L2.
 
 Prints one JSON line (rank 0).  `value` = solves per second over all ranks
 (each rank solves its own system: replicas, weak scaling).  Also reports the
@@ -16,7 +18,7 @@ end-to-end figure with host buffers, the clocks seen during the timed region
 and the FP64 CPU oracle timed on the host cores (a projection from a bounded
 sample, checked against complete 16^3 x 32 solves).  After the timed region
 the line also carries bounded measurements of the metric's other parts:
-`c3_fp16` (the same solve with IEEE FP16 storage), `c4` (16 systems on
+`c3_fx16` (the same solve with FX16 fixed-point storage), `c4` (16 systems on
 24^3 x 48 batched against one by one, and the multi-system Dslash's GB/s)
 and `c5` (a served Poisson stream: saturation, then p50 / p99 at 0.7 of it).
 
@@ -62,7 +64,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="stg", choices=["stg", "reference"])
     ap.add_argument("--lattice", default="32,32,32,64")
-    ap.add_argument("--sloppy", default="fx16", choices=["f32", "f16", "fx16", "bf16"])
+    ap.add_argument("--sloppy", default="f16", choices=["f32", "f16", "fx16", "bf16"])
     ap.add_argument("--recon", type=int, default=12, choices=[12, 18])
     ap.add_argument("--mass", type=float, default=0.005)
     ap.add_argument("--tol", type=float, default=1e-10)
@@ -86,7 +88,7 @@ def parse():
                          "batched; c5: Poisson stream of solve requests (serving); lgroup: "
                          "systems on several small lattices in one lattice-group session "
                          "against the same systems solved one by one; e1: the Dslash on the "
-                         "paper's 28^3x96 byte-model lattice in FP64/18, FP32/12, FX16/12; slabs: the "
+                         "paper's 28^3x96 byte-model lattice in FP64/18, FP32/12, FX16/12, FP16/12; slabs: the "
                          "t-slab decomposition's Dirac operation broken down as in Table 1 "
                          "(collect, exchange, compute) and its FP64 CG")
     ap.add_argument("--lg-lattices", default="8,8,8,8:8;12,12,12,24:8",
@@ -703,20 +705,23 @@ def run_c5(args):
     }), flush=True)
 
 
-def c3_fp16_measure(args, dims, U, b_np):
-    """C3 as the configuration states it: IEEE FP16 storage of links and
-    fields (per-site scale), 12-real links, FP32 compute, FP64 updates with
-    the library's FP16 default (Fig. 2 refinement, inner solves to 0.02);
-    one complete solve timed with CUDA events (its graphs captured by an
-    untimed short solve first)."""
+def c3_alt_measure(args, dims, U, b_np, storage):
+    """The C3 solve with the other 16-bit storage of 12-real links and
+    fields (`f16`: IEEE binary16 with a per-site scale, the form C3 states;
+    `fx16`: 16-bit fixed point), FP32 compute and FP64 updates with the
+    library's defaults for that storage (FP16: Fig. 2 refinement with inner
+    solves to 0.02; FX16: the Eq. 6 start and reliable updates at 0.25); one
+    complete solve timed with CUDA events (its graphs captured by an untimed
+    short solve first)."""
     import torch
     import paper_1111_0125_gb300 as stg
+    prec = {"f16": stg.STG_FP16, "fx16": stg.STG_FX16}[storage]
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.current_stream()
     b = torch.from_numpy(b_np).to(dev)
-    with stg.Gauge(dims, U, sloppy=stg.STG_FP16, recon=12) as g:
-        p = g.params(sloppy=stg.STG_FP16)
-        warm = g.params(sloppy=stg.STG_FP16, maxiter=64)
+    with stg.Gauge(dims, U, sloppy=prec, recon=12) as g:
+        p = g.params(sloppy=prec)
+        warm = g.params(sloppy=prec, maxiter=64)
         try:
             stg.stg_cg_solve(g.handle, b, torch.zeros_like(b), args.mass, args.tol, warm, stream)
         except stg.StgError:
@@ -732,7 +737,8 @@ def c3_fp16_measure(args, dims, U, b_np):
             status, st = stg.stg_status_string(err.status), err.stats
         e1.record(stream)
         torch.cuda.synchronize()
-        return {"storage": "f16 (IEEE binary16, per-site scale), 12-real links",
+        return {"storage": {"f16": "f16 (IEEE binary16, per-site scale), 12-real links",
+                            "fx16": "fx16 (16-bit fixed point, per-site scale), 12-real links"}[storage],
                 "status": status, "seconds": e0.elapsed_time(e1) / 1000.0,
                 "iters": st["iters"], "updates": st["updates"], "true_res": st["true_res"],
                 "policy": {stg.STG_CG_RELIABLE: "reliable", stg.STG_CG_REFINE: "refine"}[p.policy],
@@ -817,7 +823,7 @@ def run_lgroup(args):
 def run_e1(args):
     """The Dslash half-pass on 28^3 x 96, the lattice of the paper's byte and
     flop model (Sec. 2: 1584 B and 576 flop per site in FP64 / 18-real),
-    standalone, back to back on one stream, for FP64/18, FP32/12 and FX16/12:
+    standalone, back to back on one stream, for FP64/18, FP32/12, FX16/12 and FP16/12:
     compulsory GB/s against the measured HBM peak, the paper-model
     "effective" GB/s and GFLOP/s at 576 flop per site."""
     import torch
@@ -833,7 +839,7 @@ def run_e1(args):
     peak, peak_src = measured_hbm()
     out = {}
     for name, prec, recon in (("f64_18", stg.STG_FP64, 18), ("f32_12", stg.STG_FP32, 12),
-                              ("fx16_12", stg.STG_FX16, 12)):
+                              ("fx16_12", stg.STG_FX16, 12), ("f16_12", stg.STG_FP16, 12)):
         with stg.Gauge(dims, U, sloppy=prec, recon=recon) as g:
             fs = [g.pack(b * (1 + 0.1 * k), prec) for k in range(4)]
             o = g.new_field(prec)
@@ -855,7 +861,7 @@ def run_e1(args):
                      "gflops_576": vh * model.FLOPS_PER_SITE / t / 1e9}
     print(json.dumps({
         "metric": METRIC, "workload": "e1: Dslash half-pass on 28^3x96 (the paper's Sec. 2 lattice)",
-        "value": out["fx16_12"]["compulsory_gbs"], "unit": "GB/s", "n_gpus": 1,
+        "value": out["f16_12"]["compulsory_gbs"], "unit": "GB/s", "n_gpus": 1,
         "higher_is_better": True, "data": "synthetic", "peak": peak, "peak_source": peak_src,
         "paper_model": {"gflop_per_dslash": vh * model.FLOPS_PER_SITE / 1e9,
                         "gbyte_per_dslash_f64": model.paper_bytes_per_site("f64", 18) * vh / 1e9},
@@ -870,7 +876,7 @@ def run_slabs(args):
     undecomposed Dslash of the same lattice; then the CG of 16^3 x 32 (m =
     0.01, tol 1e-10) on 4 slabs against the undecomposed solver, in FP64 and
     with FP32 / 12-real inner iterations and FP64 reliable updates, and the
-    32^3 x 64 solve of the default workload (FX16 / 12-real inner) on 4 slabs."""
+    32^3 x 64 solve with FX16 / 12-real inner iterations on 4 slabs."""
     import torch
 
     import gen
@@ -1117,7 +1123,7 @@ def main():
     t_serial = mean_pos("t_iter_serial_ms")
     gap = max(0.0, (sum(raw.values()) - t_serial) / 4.0) if t_serial > 0 else 0.0
     cal = {k: v - gap for k, v in raw.items()}
-    staged = args.sloppy == "fx16" and args.recon == 12
+    staged = args.sloppy in ("fx16", "f16") and args.recon == 12
     kfam = ("k_dslash_fx2_staged" if staged else
             "k_dslash_fx2" if args.sloppy == "fx16" else "k_dslash")
     if cal["dslash_a"] >= cal["dslash"]:
@@ -1151,9 +1157,10 @@ def main():
     extras = {}
     if not args.no_extras and world == 1:
         # bounded measurements of the metric's other parts, after the timed
-        # region: FP16 storage as C3 states it, the batched C4 and the
-        # served C5 stream
-        extras["c3_fp16"] = c3_fp16_measure(args, dims, U, b_np)
+        # region: the other 16-bit storage, the batched C4 and the served C5
+        # stream
+        alt = "fx16" if args.sloppy == "f16" else "f16"
+        extras[f"c3_{alt}"] = c3_alt_measure(args, dims, U, b_np, alt)
         extras["c4"] = c4_measure(args, steps=2, warmup=1)
         extras["c5"] = c5_measure(args, args.c5_requests, args.c5_sat_requests, loads=[])
     cpu = None

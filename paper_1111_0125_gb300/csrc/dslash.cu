@@ -136,6 +136,11 @@ stg_status launch_dslash(const Geom &g, int prec, int epi, const DslashLaunch &L
         STG_CUDA(cudaGetLastError());
         return STG_OK;
     }
+    if (prec == P16 && recon == 12 && a.lt) {  // the same staged kernel, binary16 records
+        launch_dslash_f16_staged(epi, a, s, L.pdl);
+        STG_CUDA(cudaGetLastError());
+        return STG_OK;
+    }
     if (prec == P64) {
         if (recon == 18) launch_pr<P64, 18>(epi, a, grid, s, L.pdl);
         else launch_pr<P64, 12>(epi, a, grid, s, L.pdl);

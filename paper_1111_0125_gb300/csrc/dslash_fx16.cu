@@ -20,56 +20,63 @@
 
 namespace stg {
 
-// decode one FX16 site record already in registers
+// decode one 16-bit site record already in registers
+template <int P = PX16>
 __device__ __forceinline__ Vec3<float> fx_decode(uint4 u)
 {
     const float sc = __uint_as_float(u.w);
     Vec3<float> v;
-    v.r[0] = fx_lo(u.x) * sc; v.i[0] = fx_hi(u.x) * sc;
-    v.r[1] = fx_lo(u.y) * sc; v.i[1] = fx_hi(u.y) * sc;
-    v.r[2] = fx_lo(u.z) * sc; v.i[2] = fx_hi(u.z) * sc;
+    if constexpr (P == P16) {
+        v.r[0] = h_lo(u.x) * sc; v.i[0] = h_hi(u.x) * sc;
+        v.r[1] = h_lo(u.y) * sc; v.i[1] = h_hi(u.y) * sc;
+        v.r[2] = h_lo(u.z) * sc; v.i[2] = h_hi(u.z) * sc;
+    } else {
+        v.r[0] = fx_lo(u.x) * sc; v.i[0] = fx_hi(u.x) * sc;
+        v.r[1] = fx_lo(u.y) * sc; v.i[1] = fx_hi(u.y) * sc;
+        v.r[2] = fx_lo(u.z) * sc; v.i[2] = fx_hi(u.z) * sc;
+    }
     return v;
 }
 
 // The packed epilogue over the kernel's output field (epilogue_pair)
-template <int EPI>
+template <int EPI, int P = PX16>
 __device__ __forceinline__ f2 epilogue2(const DslashArgs &a, int iA, int iB, bool okA, bool okB,
                                         const f2 (&dr)[3], const f2 (&di)[3], float m2, uint4 wA,
                                         uint4 wB)
 {
-    return epilogue_pair<EPI>(a.out, iA, iB, okA, okB, dr, di, m2, wA, wB);
+    return epilogue_pair<EPI, P>(a.out, iA, iB, okA, okB, dr, di, m2, wA, wB);
 }
 
 // the scalar epilogue of one site (same arithmetic as k_dslash's); wraw is
 // the site's record of w, loaded at kernel start for the A epilogues
-template <int EPI>
+template <int EPI, int P = PX16>
 __device__ __forceinline__ float epilogue(const DslashArgs &a, int vh, int i, const Vec3<float> &acc,
                                           float m2, uint4 wraw)
 {
     float dot = 0.f;
     if (EPI == EPI_NONE || EPI == EPI_GATE) {
-        FieldIO<PX16>::store(a.out, vh, i, acc);
+        FieldIO<P>::store(a.out, vh, i, acc);
     } else if (EPI == EPI_RES) {
-        const Vec3<float> b = FieldIO<PX16>::load_nc(a.w, vh, i);
-        const Vec3<float> x = FieldIO<PX16>::load_nc(a.v, vh, i);
+        const Vec3<float> b = FieldIO<P>::load_nc(a.w, vh, i);
+        const Vec3<float> x = FieldIO<P>::load_nc(a.v, vh, i);
         Vec3<float> o;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             o.r[c] = b.r[c] - m2 * x.r[c] + acc.r[c];
             o.i[c] = b.i[c] - m2 * x.i[c] + acc.i[c];
         }
-        const Vec3<float> os = FieldIO<PX16>::store(a.out, vh, i, o);
+        const Vec3<float> os = FieldIO<P>::store(a.out, vh, i, o);
 #pragma unroll
         for (int c = 0; c < 3; ++c) dot += os.r[c] * os.r[c] + os.i[c] * os.i[c];
     } else {
-        const Vec3<float> d = fx_decode(wraw);
+        const Vec3<float> d = fx_decode<P>(wraw);
         Vec3<float> o;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             o.r[c] = m2 * d.r[c] - acc.r[c];
             o.i[c] = m2 * d.i[c] - acc.i[c];
         }
-        const Vec3<float> os = FieldIO<PX16>::store(a.out, vh, i, o);
+        const Vec3<float> os = FieldIO<P>::store(a.out, vh, i, o);
 #pragma unroll
         for (int c = 0; c < 3; ++c) dot += d.r[c] * os.r[c] + d.i[c] * os.i[c];
     }
@@ -78,11 +85,11 @@ __device__ __forceinline__ float epilogue(const DslashArgs &a, int vh, int i, co
 
 // D chi = (P - N) / 32767 of both sites, negated for the A epilogues, then
 // the packed epilogue
-template <int EPI>
+template <int EPI, int P = PX16>
 __device__ __forceinline__ f2 finish_pair(const DslashArgs &a, int iA, int iB, bool okA, bool okB,
                                           const Acc2 &A, float m2, uint4 wA, uint4 wB)
 {
-    const f2 k = make_float2(LinkPost<PX16>::k, LinkPost<PX16>::k);
+    const f2 k = make_float2(LinkPost<P>::k, LinkPost<P>::k);
     constexpr bool neg = (EPI == EPI_A || EPI == EPI_A_DOT || EPI == EPI_A_CG);
     f2 dr[3], di[3];
 #pragma unroll
@@ -90,7 +97,7 @@ __device__ __forceinline__ f2 finish_pair(const DslashArgs &a, int iA, int iB, b
         dr[c] = mul2(A.re[c], neg ? neg2(k) : k);
         di[c] = mul2(A.im[c], neg ? neg2(k) : k);
     }
-    return epilogue2<EPI>(a, iA, iB, okA, okB, dr, di, m2, wA, wB);
+    return epilogue2<EPI, P>(a, iA, iB, okA, okB, dr, di, m2, wA, wB);
 }
 
 template <int R, int EPI>
@@ -220,7 +227,7 @@ __device__ __forceinline__ void fill_stage(const char *lt, char *stage, unsigned
               &full[st]);
 }
 
-template <int EPI>
+template <int P, int EPI>
 __global__ void __launch_bounds__(kFxCons, kFxCtasPerSM) k_dslash_fx2_staged(const DslashArgs a)
 {
     extern __shared__ __align__(128) char stage[];
@@ -311,12 +318,12 @@ __global__ void __launch_bounds__(kFxCons, kFxCtasPerSM) k_dslash_fx2_staged(con
             float sfA, sbA, sfB, sbB;
             link_signs(a.g, sA, mu, sfA, sbA);
             link_signs(a.g, sB, mu, sfB, sbB);
-            const float k = LinkPost<PX16>::row2;
+            const float k = LinkPost<P>::row2;
             const f2 s2f = make_float2(sfA * k, sfB * k);
             const f2 s2b = make_float2(sbA * k, sbB * k);
             Vec3x2 vf, vb;
-            load_field2(a.in, jfA, jfB, vf);
-            load_field2(a.in, jbA, jbB, vb);
+            load_field2<P>(a.in, jfA, jfB, vf);
+            load_field2<P>(a.in, jbA, jbB, vb);
             const int q = 4 * j + mu;          // item number
             const int sq = q % kFxStages;      // its ring stage
             const bool ready = mbar_wait(smem_addr(&full[sq]), (unsigned)(q / kFxStages) & 1u, abort,
@@ -352,9 +359,9 @@ __global__ void __launch_bounds__(kFxCons, kFxCtasPerSM) k_dslash_fx2_staged(con
                 }
             }
             Mat3x2 u;
-            decode12(fa, fb, fc, fd, u);
+            decode12<P>(fa, fb, fc, fd, u);
             fwd2<12>(u, vf, s2f, A);
-            decode12(ba, bb, bc, bd, u);
+            decode12<P>(ba, bb, bc, bd, u);
             bwd2<12>(u, vb, s2b, A);
         }
         if (!alive) {
@@ -364,7 +371,7 @@ __global__ void __launch_bounds__(kFxCons, kFxCtasPerSM) k_dslash_fx2_staged(con
         const float m2 = (EPI == EPI_A_CG) ? float(a.state->m2) : float(a.m2);
         f2 dA_B;
         if (EPI == EPI_RES) {
-            const f2 kk = make_float2(LinkPost<PX16>::k, LinkPost<PX16>::k);
+            const f2 kk = make_float2(LinkPost<P>::k, LinkPost<P>::k);
             Vec3<float> accA, accB;
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
@@ -375,10 +382,10 @@ __global__ void __launch_bounds__(kFxCons, kFxCtasPerSM) k_dslash_fx2_staged(con
                 accB.r[q] = re.y;
                 accB.i[q] = im.y;
             }
-            dA_B.x = okA ? epilogue<EPI>(a, vh, iA, accA, m2, wA) : 0.f;
-            dA_B.y = okB ? epilogue<EPI>(a, vh, iB, accB, m2, wB) : 0.f;
+            dA_B.x = okA ? epilogue<EPI, P>(a, vh, iA, accA, m2, wA) : 0.f;
+            dA_B.y = okB ? epilogue<EPI, P>(a, vh, iB, accB, m2, wB) : 0.f;
         } else {
-            dA_B = finish_pair<EPI>(a, iA, iB, okA, okB, A, m2, wA, wB);
+            dA_B = finish_pair<EPI, P>(a, iA, iB, okA, okB, A, m2, wA, wB);
             if (!okA) dA_B.x = 0.f;
             if (!okB) dA_B.y = 0.f;
         }
@@ -411,12 +418,12 @@ __global__ void __launch_bounds__(kFxCons, kFxCtasPerSM) k_dslash_fx2_staged(con
     }
 }
 
-template <int EPI>
+template <int P, int EPI>
 static void launch_staged(const DslashArgs &a, cudaStream_t s, bool pdl)
 {
     // set once per instantiation (thread-safe static initialisation)
     static const int sms = [] {
-        cudaFuncSetAttribute(k_dslash_fx2_staged<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_dslash_fx2_staged<P, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)kFxSmem);
         int dev = 0, n = 0;
         cudaGetDevice(&dev);
@@ -431,7 +438,7 @@ static void launch_staged(const DslashArgs &a, cudaStream_t s, bool pdl)
     if (a.grid_cap > 0 && a.grid_cap < cap) cap = a.grid_cap;
     const int ntiles = (a.g.Vh + kFxTile - 1) / kFxTile;
     const int grid = ntiles < cap ? ntiles : cap;
-    launch_k(k_dslash_fx2_staged<EPI>, grid, kFxCons, kFxSmem, s, pdl, a);
+    launch_k(k_dslash_fx2_staged<P, EPI>, grid, kFxCons, kFxSmem, s, pdl, a);
 }
 
 template <int R>
@@ -447,17 +454,30 @@ static void launch_r(int epi, const DslashArgs &a, int grid, cudaStream_t s, boo
     }
 }
 
+template <int P>
+static void launch_staged_p(int epi, const DslashArgs &a, cudaStream_t s, bool pdl)
+{
+    switch (epi) {
+    case EPI_NONE: launch_staged<P, EPI_NONE>(a, s, pdl); break;
+    case EPI_A: launch_staged<P, EPI_A>(a, s, pdl); break;
+    case EPI_A_DOT: launch_staged<P, EPI_A_DOT>(a, s, pdl); break;
+    case EPI_A_CG: launch_staged<P, EPI_A_CG>(a, s, pdl); break;
+    case EPI_RES: launch_staged<P, EPI_RES>(a, s, pdl); break;
+    case EPI_GATE: launch_staged<P, EPI_GATE>(a, s, pdl); break;
+    }
+}
+
+// IEEE FP16 / 12-real links in the tile-major copy: the staged kernel with
+// binary16 decode and encode
+void launch_dslash_f16_staged(int epi, const DslashArgs &a, cudaStream_t s, bool pdl)
+{
+    launch_staged_p<P16>(epi, a, s, pdl);
+}
+
 void launch_dslash_fx2(int recon, int epi, const DslashArgs &a, cudaStream_t s, bool pdl)
 {
     if (recon == 12 && a.lt) {
-        switch (epi) {
-        case EPI_NONE: launch_staged<EPI_NONE>(a, s, pdl); break;
-        case EPI_A: launch_staged<EPI_A>(a, s, pdl); break;
-        case EPI_A_DOT: launch_staged<EPI_A_DOT>(a, s, pdl); break;
-        case EPI_A_CG: launch_staged<EPI_A_CG>(a, s, pdl); break;
-        case EPI_RES: launch_staged<EPI_RES>(a, s, pdl); break;
-        case EPI_GATE: launch_staged<EPI_GATE>(a, s, pdl); break;
-        }
+        launch_staged_p<PX16>(epi, a, s, pdl);
         return;
     }
     const int grid = (a.g.Vh + 2 * kBlock - 1) / (2 * kBlock);

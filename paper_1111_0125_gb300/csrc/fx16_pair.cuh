@@ -1,14 +1,16 @@
-// Two sites (or two systems) per thread on packed FP32x2 arithmetic for
-// FX16 (16-bit fixed point) storage: the .x half of every float2 holds one
-// site's value and the .y half the other's, and every FP32 operation is one
-// sm_100 FP32x2 instruction (__ffma2_rn, __fadd2_rn, __fmul2_rn) for both.
-// Shared by the single-system FX16 Dslash (dslash_fx16.cu) and the staged
-// multi-system kernel with site pairs (mrhs_paired.cuh).
+// Two sites (or two systems) per thread on packed FP32x2 arithmetic for the
+// 16-bit storage forms FX16 (16-bit fixed point; the default template
+// argument P) and IEEE FP16 (P16, per-site field scale, unscaled links): the
+// .x half of every float2 holds one site's value and the .y half the
+// other's, and every FP32 operation is one sm_100 FP32x2 instruction
+// (__ffma2_rn, __fadd2_rn, __fmul2_rn) for both.  Shared by the single-system
+// 16-bit Dslash (dslash_fx16.cu) and the staged multi-system kernel with site
+// pairs (mrhs_paired.cuh).
 //
-// Links are integer-valued floats (32767 U); a kernel scales its sum by
-// 1/32767 at the end, and the 12-real row 2 c = r0 x r1 enters the products
-// with the factor s / 32767 (s the folded phase), i.e. U_2b = (s / 32767)
-// conj(c_b).  Each colour keeps one real and one imaginary accumulator; the
+// FX16 links are integer-valued floats (32767 U); a kernel scales its sum by
+// 1/32767 at the end (LinkPost<P>::k), and the 12-real row 2 c = r0 x r1
+// enters the products with the factor s LinkPost<P>::row2 (s the folded
+// phase), i.e. U_2b = (s / 32767) conj(c_b); FP16 links carry U itself.  Each colour keeps one real and one imaginary accumulator; the
 // signs of the products are carried by negated FP32x2 operands, which cost
 // no instruction.
 #pragma once
@@ -39,23 +41,42 @@ struct Vec3x2 {
     f2 r[3], i[3];
 };
 
-__device__ __forceinline__ void set2(Mat3x2 &u, int k, unsigned wa, unsigned wb)
+// the halves of one binary16 word as floats
+__device__ __forceinline__ float h_lo(unsigned w) { return __half2float(__ushort_as_half((unsigned short)(w & 0xFFFFu))); }
+__device__ __forceinline__ float h_hi(unsigned w) { return __half2float(__ushort_as_half((unsigned short)(w >> 16))); }
+
+// one (re, im) word of site A (wa) and of site B (wb) as (A, B) pairs
+template <int P = PX16>
+__device__ __forceinline__ void word2(unsigned wa, unsigned wb, f2 &re, f2 &im)
 {
-    u.r[k / 3][k % 3] = unbias(fxb_lo(wa), fxb_lo(wb));
-    u.i[k / 3][k % 3] = unbias(fxb_hi(wa), fxb_hi(wb));
+    static_assert(P == PX16 || P == P16, "16-bit pair forms: FX16 and FP16");
+    if constexpr (P == PX16) {
+        re = unbias(fxb_lo(wa), fxb_lo(wb));
+        im = unbias(fxb_hi(wa), fxb_hi(wb));
+    } else {
+        re = make_float2(h_lo(wa), h_lo(wb));
+        im = make_float2(h_hi(wa), h_hi(wb));
+    }
 }
 
-// 12-real: row 2 is c = r0 x r1 (no conjugate, no sign, 32767^2 scale);
+template <int P = PX16>
+__device__ __forceinline__ void set2(Mat3x2 &u, int k, unsigned wa, unsigned wb)
+{
+    word2<P>(wa, wb, u.r[k / 3][k % 3], u.i[k / 3][k % 3]);
+}
+
+// 12-real: row 2 is c = r0 x r1 (no conjugate, no sign; FX16: 32767^2 scale);
 // a / b hold rows 0-1 entries 0-3 of sites A / B, c / d entries 4-5
+template <int P = PX16>
 __device__ __forceinline__ void decode12(const uint4 &a, const uint4 &b, const uint2 &c, const uint2 &d,
                                          Mat3x2 &u)
 {
-    set2(u, 0, a.x, b.x);
-    set2(u, 1, a.y, b.y);
-    set2(u, 2, a.z, b.z);
-    set2(u, 3, a.w, b.w);
-    set2(u, 4, c.x, d.x);
-    set2(u, 5, c.y, d.y);
+    set2<P>(u, 0, a.x, b.x);
+    set2<P>(u, 1, a.y, b.y);
+    set2<P>(u, 2, a.z, b.z);
+    set2<P>(u, 3, a.w, b.w);
+    set2<P>(u, 4, c.x, d.x);
+    set2<P>(u, 5, c.y, d.y);
 #pragma unroll
     for (int a2 = 0; a2 < 3; ++a2) {
         const int b2 = (a2 + 1) % 3, c2 = (a2 + 2) % 3;
@@ -106,17 +127,23 @@ __device__ __forceinline__ void load_link2(const char *blk, int vh, int sa, int 
 // K s precomputed, is exact for the 15-bit scales of fx_scale and saves an
 // instruction, but measured about 1% slower on the half-pass: it puts the
 // multiply K s on the critical path of every neighbour.)
+// (FP16: the binary16 value times the site's scale, as FieldIO<P16>)
+template <int P = PX16>
 __device__ __forceinline__ void load_field2(const void *f, int sa, int sb, Vec3x2 &v)
 {
     const uint4 *p = static_cast<const uint4 *>(f);
     const uint4 a = __ldg(p + sa), b = __ldg(p + sb);
     const f2 sc = make_float2(__uint_as_float(a.w), __uint_as_float(b.w));
-    v.r[0] = mul2(unbias(fxb_lo(a.x), fxb_lo(b.x)), sc);
-    v.i[0] = mul2(unbias(fxb_hi(a.x), fxb_hi(b.x)), sc);
-    v.r[1] = mul2(unbias(fxb_lo(a.y), fxb_lo(b.y)), sc);
-    v.i[1] = mul2(unbias(fxb_hi(a.y), fxb_hi(b.y)), sc);
-    v.r[2] = mul2(unbias(fxb_lo(a.z), fxb_lo(b.z)), sc);
-    v.i[2] = mul2(unbias(fxb_hi(a.z), fxb_hi(b.z)), sc);
+    f2 r, i;
+    word2<P>(a.x, b.x, r, i);
+    v.r[0] = mul2(r, sc);
+    v.i[0] = mul2(i, sc);
+    word2<P>(a.y, b.y, r, i);
+    v.r[1] = mul2(r, sc);
+    v.i[1] = mul2(i, sc);
+    word2<P>(a.z, b.z, r, i);
+    v.r[2] = mul2(r, sc);
+    v.i[2] = mul2(i, sc);
 }
 
 // D chi accumulated as (re, im) per colour; the signs of the products sit
@@ -190,9 +217,24 @@ __device__ __forceinline__ void bwd2(const Mat3x2 &u, const Vec3x2 &v, f2 s2, Ac
 // decode the FX16 records of sites A and B into .x / .y: (K + q) s - K s as
 // one FMA per pair with K s precomputed, exact (one rounding, bitwise q * s)
 // because fx_scale keeps 15 significant bits and K = 1.5 * 2^23 + 32768 has 9
+// (FP16: the binary16 values times the sites' scales, as FieldIO<P16>)
+template <int P = PX16>
 __device__ __forceinline__ void decode_fx2(const uint4 &a, const uint4 &b, f2 (&r)[3], f2 (&im)[3])
 {
     const f2 sc = make_float2(__uint_as_float(a.w), __uint_as_float(b.w));
+    if constexpr (P == P16) {
+        f2 x, y;
+        word2<P>(a.x, b.x, x, y);
+        r[0] = mul2(x, sc);
+        im[0] = mul2(y, sc);
+        word2<P>(a.y, b.y, x, y);
+        r[1] = mul2(x, sc);
+        im[1] = mul2(y, sc);
+        word2<P>(a.z, b.z, x, y);
+        r[2] = mul2(x, sc);
+        im[2] = mul2(y, sc);
+        return;
+    }
     const f2 nks = mul2(sc, make_float2(-12615680.f, -12615680.f));
     r[0] = fma2(make_float2(fxb_lo(a.x), fxb_lo(b.x)), sc, nks);
     im[0] = fma2(make_float2(fxb_hi(a.x), fxb_hi(b.x)), sc, nks);
@@ -205,8 +247,30 @@ __device__ __forceinline__ void decode_fx2(const uint4 &a, const uint4 &b, f2 (&
 // encode sites A (.x) and B (.y) as FX16 records (the scale and the
 // NaN-propagating maximum of FieldIO<PX16>::store; the scaled value plus the
 // offset rounded once by one FMA)
+// (FP16: the scale is the site's largest |component| and the record holds
+// the components over it in binary16, as FieldIO<P16>::store)
+template <int P = PX16>
 __device__ __forceinline__ void encode_fx2(const f2 (&r)[3], const f2 (&im)[3], uint4 &ua, uint4 &ub)
 {
+    if constexpr (P == P16) {
+        float mA = 0.f, mB = 0.f;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            mA = fmaxf(mA, fmaxf(fabsf(r[c].x), fabsf(im[c].x)));
+            mB = fmaxf(mB, fmaxf(fabsf(r[c].y), fabsf(im[c].y)));
+        }
+        const f2 inv = make_float2(mA > 0.f ? 1.0f / mA : 0.f, mB > 0.f ? 1.0f / mB : 0.f);
+        unsigned wa[3], wb[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const f2 sr = mul2(r[c], inv), si = mul2(im[c], inv);
+            wa[c] = f2_to_h2(sr.x, si.x);
+            wb[c] = f2_to_h2(sr.y, si.y);
+        }
+        ua = make_uint4(wa[0], wa[1], wa[2], __float_as_uint(mA));
+        ub = make_uint4(wb[0], wb[1], wb[2], __float_as_uint(mB));
+        return;
+    }
     float mA = 0.f, mB = 0.f;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -231,7 +295,7 @@ __device__ __forceinline__ void encode_fx2(const f2 (&r)[3], const f2 (&im)[3], 
 // -D chi for the A epilogues (nacc), which then form q = m^2 w - D chi as
 // one FMA.  Stores the sites that exist; returns the pair of site terms of
 // Re w^dag q (q as stored) for EPI_A_DOT / EPI_A_CG.  EPI_RES is not packed.
-template <int EPI>
+template <int EPI, int P = PX16>
 __device__ __forceinline__ f2 epilogue_pair(void *out_field, int iA, int iB, bool okA, bool okB,
                                             const f2 (&dr)[3], const f2 (&di)[3], float m2, uint4 wA,
                                             uint4 wB)
@@ -240,12 +304,12 @@ __device__ __forceinline__ f2 epilogue_pair(void *out_field, int iA, int iB, boo
     f2 dot = make_float2(0.f, 0.f);
     if (EPI == EPI_NONE || EPI == EPI_GATE) {
         uint4 ua, ub;
-        encode_fx2(dr, di, ua, ub);
+        encode_fx2<P>(dr, di, ua, ub);
         if (okA) out[iA] = ua;
         if (okB) out[iB] = ub;
     } else {
         f2 wr[3], wi[3], qr[3], qi[3];
-        decode_fx2(wA, wB, wr, wi);
+        decode_fx2<P>(wA, wB, wr, wi);
         const f2 mm = make_float2(m2, m2);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -253,12 +317,12 @@ __device__ __forceinline__ f2 epilogue_pair(void *out_field, int iA, int iB, boo
             qi[c] = fma2(mm, wi[c], di[c]);
         }
         uint4 ua, ub;
-        encode_fx2(qr, qi, ua, ub);
+        encode_fx2<P>(qr, qi, ua, ub);
         if (okA) out[iA] = ua;
         if (okB) out[iB] = ub;
         if (EPI == EPI_A_DOT || EPI == EPI_A_CG) {
             f2 sr[3], si[3];
-            decode_fx2(ua, ub, sr, si);
+            decode_fx2<P>(ua, ub, sr, si);
             dot = mul2(wr[0], sr[0]);
             dot = fma2(wi[0], si[0], dot);
 #pragma unroll

@@ -290,8 +290,9 @@ static bool want_mtiled()
     return !(v && v[0] == '0');
 }
 
-// The staged FX16 / 12-real Dslash is the default; STG_FX16_TILED=0 at gauge
-// creation keeps the register-fed kernel (no tile-major copy).
+// The staged FX16 / FP16 12-real Dslash is the default; STG_FX16_TILED=0 at
+// gauge creation keeps the register-fed (FX16) or one-site (FP16) kernel (no
+// tile-major copy).
 static bool want_tiled()
 {
     const char *v = getenv("STG_FX16_TILED");
@@ -384,7 +385,7 @@ size_t gauge_bytes(const int dims[4], int sloppy, int recon)
     const int recon_hi = (sloppy == P64) ? recon : 18;
     size_t n = 8 * align256(vh * link_bytes(P64, recon_hi));
     if (sloppy != P64) n += 8 * align256(vh * link_bytes(sloppy, recon));
-    if (sloppy == PX16 && recon == 12 && want_tiled())
+    if ((sloppy == PX16 || sloppy == P16) && recon == 12 && want_tiled())
         n += 2 * (size_t)((g.Vh + kFxTile - 1) / kFxTile) * 4 * kFxStageBytes;
     if ((sloppy == P32 || sloppy == PX16) && recon == 12 && want_mtiled())
         n += 2 * (size_t)((g.Vh + kMTile - 1) / kMTile) * kMTile * 8 * (sloppy == P32 ? 48 : 24);
@@ -422,7 +423,7 @@ stg_status gauge_create(const int dims[4], const double *links_host, int sloppy,
     const int recon_hi = (sloppy == P64) ? recon : 18;
     if (st == STG_OK) st = pack_links(g->geom, ucan, P64, recon_hi, &g->hi, s);
     if (st == STG_OK && sloppy != P64) st = pack_links(g->geom, ucan, sloppy, recon, &g->lo, s);
-    if (st == STG_OK && sloppy == PX16 && recon == 12 && want_tiled()) {
+    if (st == STG_OK && (sloppy == PX16 || sloppy == P16) && recon == 12 && want_tiled()) {
         st = tile_links(g->geom, &g->lo, s);
         read_fx_hooks(&g->lo);
     }

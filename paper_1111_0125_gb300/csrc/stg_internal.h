@@ -34,7 +34,7 @@ static inline cudaError_t launch_k(void (*kernel)(K...), dim3 grid, dim3 block, 
 }
 
 // Device copy of the links in one precision / reconstruction.
-// Tile-major copy of FX16 / 12-real links for the staged Dslash: for output
+// Tile-major copy of FX16 or FP16 / 12-real links for the staged Dslash: for output
 // parity p, tile k of kFxTile consecutive output sites and direction mu, one
 // contiguous block of kFxStageBytes holds the forward links U_mu(x) (uint4
 // [kFxTile] then uint2 [kFxTile]) followed by the backward links U_mu(x - mu)
@@ -197,6 +197,8 @@ struct DslashArgs {
 
 // FX16 Dslash, two sites per thread on packed FP32x2 arithmetic
 void launch_dslash_fx2(int recon, int epi, const DslashArgs &a, cudaStream_t s, bool pdl);
+// IEEE FP16 / 12-real with the tile-major links: the same staged kernel
+void launch_dslash_f16_staged(int epi, const DslashArgs &a, cudaStream_t s, bool pdl);
 
 int grid_for(long n);
 

@@ -3,9 +3,10 @@ times.
 
 * 32^3 x 64, exp(i 0.6 H) links, m = 0.005: Dslash outputs at sampled sites
   (random plus every boundary class) against the oracle evaluated site by
-  site, for FX16/12 (the bench's inner precision), FP32/12 and FP64/18; the
-  bench's mixed CG solve to 1e-10 checked with the oracle's A on the whole
-  lattice (a property that holds at any size).
+  site, for FP16/12 (the bench's inner precision), FX16/12, FP32/12 and
+  FP64/18; the bench's mixed CG solve (FP16 and FX16 inner) to 1e-10 checked
+  with the oracle's A on the whole lattice (a property that holds at any
+  size).
 * 16^3 x 32, exp(i 0.4 H), m = 0.01: mixed FP32 CG and plain FP64 CG both
   reach a 1e-10 true residual (oracle's A) and agree within kappa * tol.
 * 24^3 x 48, exp(i 0.5 H): sampled Dslash parity.
@@ -52,7 +53,7 @@ def _rel_rows(a, b):
 
 
 @pytest.mark.parametrize("dims,eps", [((32, 32, 32, 64), 0.6), ((24, 24, 24, 48), 0.5)])
-@pytest.mark.parametrize("prec,recon", [(stg.STG_FX16, 12), (stg.STG_FP32, 12),
+@pytest.mark.parametrize("prec,recon", [(stg.STG_FP16, 12), (stg.STG_FX16, 12), (stg.STG_FP32, 12),
                                         (stg.STG_FP64, 18)])
 def test_dslash_sampled_sites(dims, eps, prec, recon):
     U = _gauge(dims, eps)
@@ -67,15 +68,16 @@ def test_dslash_sampled_sites(dims, eps, prec, recon):
             assert _rel_rows(out[sites], want) < TOL[prec], (prec, recon, parity)
 
 
-def test_bench_workload_mixed_cg_32x64():
-    """The bench's solve: FX16/12 inner iterations, FP64 reliable updates,
-    m = 0.005, tol = 1e-10, source seed 1."""
+@pytest.mark.parametrize("prec", [stg.STG_FP16, stg.STG_FX16])
+def test_bench_workload_mixed_cg_32x64(prec):
+    """The bench's solve: FP16/12 inner iterations (and FX16/12 beside it)
+    with the library's default updates, m = 0.005, tol = 1e-10, source
+    seed 1."""
     dims, mass, tol = (32, 32, 32, 64), 0.005, 1e-10
     U = _gauge(dims, 0.6)
     b = gen.source(dims, seed=1)
-    with stg.Gauge(dims, U, sloppy=stg.STG_FX16, recon=12) as g:
-        x, st = g.cg_solve(torch.from_numpy(b).cuda(), mass, tol,
-                           g.params(policy=stg.STG_CG_RELIABLE, timing=1))
+    with stg.Gauge(dims, U, sloppy=prec, recon=12) as g:
+        x, st = g.cg_solve(torch.from_numpy(b).cuda(), mass, tol, g.params(timing=1))
     x = x.cpu().numpy()
     r = b - oracle.apply_A(dims, U, mass, x)
     tr = np.linalg.norm(r) / np.linalg.norm(b)
@@ -106,7 +108,7 @@ def test_c2_mixed_vs_fp64_16x32():
     assert 0 < sm["updates"] < sm["iters"]
 
 
-@pytest.mark.parametrize("prec", [stg.STG_FX16, stg.STG_FP32])
+@pytest.mark.parametrize("prec", [stg.STG_FP16, stg.STG_FX16, stg.STG_FP32])
 def test_dot_reduction_against_exact_sum_32x64(prec):
     """d^dag A d of stg_apply_A_dot at 32^3 x 64 (the reduction of the CG's
     alpha, and the same grid_sum_ff code as its |r|^2) against the exact sum.

@@ -60,6 +60,8 @@ def test_dslash_mrhs_matches_oracle_and_single(dims, prec, recon, n):
         nb, tps = stg.stg_mrhs_tuning(g.handle, prec, n)
         if tps == 0:  # staged kernel (12-real only)
             assert recon == 12 and nb in (2, 4, 8)
+        elif tps == -1:  # staged, two sites per thread (FX16 / 12-real only)
+            assert prec == stg.STG_FX16 and recon == 12 and nb in (2, 4)
         else:
             assert nb in (1, 2, 4) and tps in (1, 2, 4, 8, 16) and tps <= max(1, n)
 

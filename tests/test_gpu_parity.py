@@ -202,6 +202,50 @@ def test_gauge_create_rejects_bad_dims():
     assert e.value.status == stg.STG_ERR_DIMS
 
 
+@pytest.mark.parametrize("grid", ["3", None])
+def test_staged_fp16_matches_one_site_kernel(monkeypatch, grid):
+    """IEEE FP16 / 12-real links also go through the staged two-site kernel
+    (binary16 decode and encode in place of the fixed-point ones).  Against
+    the one-site-per-thread FP16 kernel (gauge created with STG_FX16_TILED=0)
+    it differs only by rounding order: both within FP16's tolerance of the
+    oracle and within 2e-3 of each other; A, d^dag A d and a CG solve on the
+    staged path agree with the oracle."""
+    dims, mass = (12, 12, 12, 24), 0.05
+    U = _links(dims, "exp", seed=4, eps=0.5)
+    chi = gen.source(dims, seed=9)
+    if grid is not None:
+        monkeypatch.setenv("STG_FX16_GRID", grid)
+    monkeypatch.setenv("STG_FX16_TILED", "0")
+    plain = Gauge(dims, U, sloppy=stg.STG_FP16, recon=12)
+    monkeypatch.delenv("STG_FX16_TILED")
+    staged = Gauge(dims, U, sloppy=stg.STG_FP16, recon=12)
+    try:
+        P = stg.STG_FP16
+        assert stg.stg_gauge_bytes(dims, P, 12) > stg.stg_gauge_bytes(dims, stg.STG_FP32, 18) // 4
+        fp, fs = plain.pack(_to_dev(chi), P), staged.pack(_to_dev(chi), P)
+        assert torch.equal(fp, fs)
+        for parity in (0, 1):
+            a = plain.unpack(plain.dslash(fp, parity, P), P).cpu().numpy()
+            b = staged.unpack(staged.dslash(fs, parity, P), P).cpu().numpy()
+            ref = oracle.dslash(dims, U, chi, parity)
+            assert rel(b, ref) < TOL[P] and rel(a, ref) < TOL[P]
+            assert rel(b, a) < 2e-3
+        as_, ds = staged.apply_A_dot(fs, mass, P)
+        out = staged.unpack(as_, P).cpu().numpy()
+        ref = oracle.apply_A(dims, U, mass, chi)
+        assert rel(out, ref) < TOL[P]
+        ref_dot = float(np.vdot(chi, ref).real)
+        assert abs(ds.item() - ref_dot) < 1e-2 * abs(ref_dot)
+        b = gen.source(dims, seed=10)
+        x, st = staged.cg_solve(_to_dev(b), mass, 1e-10)
+        assert st["true_res"] <= 1e-10
+        res = np.linalg.norm(b - oracle.apply_A(dims, U, mass, x.cpu().numpy())) / np.linalg.norm(b)
+        assert res <= 1.01e-10
+    finally:
+        plain.close()
+        staged.close()
+
+
 @pytest.mark.parametrize("grid", ["1", "4", "7", None])
 def test_staged_fx16_tiles_per_cta(monkeypatch, grid):
     """The staged FX16/12 Dslash (tile-major links streamed through shared

@@ -4,9 +4,10 @@
   reconstruction, P from 1 (self-exchange) to one slab of two time slices
   per rank, both parities; the two edge slices of every slab (where the
   ghost fields and ghost links are read) are also checked on their own.
-- FP64, FP32, FP16 and BF16 are bitwise equal to stg_dslash on the whole
-  lattice: the same arithmetic in the same order, only the source of the
-  neighbour data differs.
+- FP64, FP32, BF16 and FP16 / 18-real are bitwise equal to stg_dslash on
+  the whole lattice: the same arithmetic in the same order, only the source
+  of the neighbour data differs (FX16 and FP16 with 12-real links run the
+  staged two-site kernel there).
 - COPY, DIRECT and the overlapped schedule give bitwise the same output and
   the same d^dag A d.
 - apply_A_dot against the oracle's A and its inner product.
@@ -106,7 +107,7 @@ def test_slab_dslash_matches_oracle(dims, counts, prec, recon):
         chi = gen.source(dims, seed=11 + parity)
         ref = oracle.dslash(dims, U, chi, parity)
         whole = None
-        if prec != stg.STG_FX16:
+        if prec != stg.STG_FX16 and not (prec == stg.STG_FP16 and recon == 12):
             with Gauge(dims, U, sloppy=prec, recon=recon) as g:
                 whole = g.unpack(g.dslash(g.pack(_to_dev(chi), prec), parity, prec), prec)
                 whole = whole.cpu().numpy()
