@@ -426,7 +426,7 @@ def config_dict(args, dims):
     return {"workload": workload_name(dims, args.tol), "lattice": "x".join(str(d) for d in dims),
             "mass": args.mass, "tol": args.tol, "links": f"exp(i*{args.eps}*H) SU(3), seed 0",
             "source": "complex Gaussian, seed 1+rank", "sloppy_storage": args.sloppy,
-            "compute": "f32 inner iterations; f64 reliable updates and grid sums",
+            "compute": "f32 inner iterations; f64 true-residual updates and grid sums",
             "recon": args.recon, "reliable_delta": args.delta, "policy": args.policy,
             "l2": "inputs larger than L2 (links alone exceed 129 MB); no flush",
             "parallelism": f"replicas{args.gpus}"}
