@@ -528,6 +528,7 @@ def c4_measure(args, steps, warmup, one_by_one_reps=1):
         "mrhs_dslash": {"rhs_block": nb, "threads_per_site": tb,
                         "kernel": ("k_dslash_ms (staged)" if tb == 0 else
                                    "k_dslash_msp (staged, two sites per thread)" if tb == -1
+                                   else "k_dslash_ms (staged, (re, im) FP32x2 pairs)" if tb == -2
                                    else "k_dslash_m"),
                         "launch_ms": t_m,
                         "algorithmic_bytes_per_launch": nbytes,

@@ -52,10 +52,14 @@ static bool same_key(const TuneEntry &e, const int *dims, int prec, int recon, i
 // shapes 0 .. kMrhsShapes - 1: register-fed (NB, TPS); then the staged
 // kernel with NB = ms_nb(shape - kMrhsShapes) (12-real FP32 / FX16 links);
 // then (FX16 / 12-real only) the staged kernel with two sites per thread,
-// NB = msp_nb(shape - kMrhsShapes - kMrhsStagedShapes)
+// NB = msp_nb(shape - kMrhsShapes - kMrhsStagedShapes); then (FP32 / 12-real
+// only) the staged kernel on (re, im) FP32x2 pairs, NB = ms_ri_nb(shape -
+// kRiFirst)
 constexpr int kMspFirst = kMrhsShapes + kMrhsStagedShapes;
-constexpr int kMspCount = 2;  // NB = 2, 4 (mrhs_paired.cuh)
-static bool valid_choice(int shape) { return shape >= 0 && shape < kMspFirst + kMspCount; }
+constexpr int kMspCount = kMspShapes;  // NB = 2, 4 (mrhs_paired.cuh)
+constexpr int kRiFirst = kMsRiFirst;
+constexpr int kNumShapes = kRiFirst + kMsRiShapes;
+static bool valid_choice(int shape) { return shape >= 0 && shape < kNumShapes; }
 
 static bool staged_ok(const LinkField *lf)
 {
@@ -66,7 +70,8 @@ static bool shape_ok(const LinkField *lf, int shape)
 {
     if (shape < kMrhsShapes) return true;
     if (shape < kMspFirst) return staged_ok(lf);
-    return staged_ok(lf) && lf->prec == PX16;
+    if (shape < kRiFirst) return staged_ok(lf) && lf->prec == PX16;
+    return staged_ok(lf) && lf->prec == P32;
 }
 
 static void tune_load_file_locked()
@@ -142,7 +147,7 @@ static stg_status launch_m(const stg_gauge *g, const LinkField *lf, int shape, i
     if (shape >= kMrhsShapes) {
         if (!shape_ok(lf, shape)) {
             set_error("multi-system Dslash: the staged kernel needs the tile-major 12-real links "
-                      "(FP32 or FX16; two sites per thread: FX16)");
+                      "(FP32 or FX16; two sites per thread: FX16; (re, im) pairs: FP32)");
             return STG_ERR_UNSUPPORTED;
         }
         a.lt = lf->mtiled + (size_t)a.parity * lf->mtiled_parity_bytes;
@@ -190,7 +195,7 @@ static stg_status tune(const stg_gauge *g, const LinkField *lf, int n, const voi
     float best = 1e30f;
     int bshape = 0;
     stg_status st = STG_OK;
-    for (int k = 0; k < kMspFirst + kMspCount && st == STG_OK; ++k) {
+    for (int k = 0; k < kNumShapes && st == STG_OK; ++k) {
         if (k < kMrhsShapes) {
             if (mrhs_tps(k) > n || (mrhs_tps(k) == 1 && mrhs_nb(k) > n && mrhs_nb(k) > 1)) continue;
         } else if (k < kMspFirst) {
@@ -198,10 +203,13 @@ static stg_status tune(const stg_gauge *g, const LinkField *lf, int n, const voi
             // larger than a group's share only adds idle slots
             const int nb = ms_nb(k - kMrhsShapes);
             if (!staged_ok(lf) || (nb > 2 && nb > (n + kMsGroups - 1) / kMsGroups)) continue;
-        } else {
+        } else if (k < kRiFirst) {
             // four warps share the systems (two sites per thread)
             const int nb = k == kMspFirst ? 2 : 4;
             if (!shape_ok(lf, k) || (nb > 2 && nb > (n + 3) / 4)) continue;
+        } else {
+            const int nb = ms_ri_nb(k - kRiFirst);
+            if (!shape_ok(lf, k) || (nb > 2 && nb > (n + kMsGroups - 1) / kMsGroups)) continue;
         }
         MrhsArgs a = {};
         a.parity = 1;
@@ -917,7 +925,10 @@ stg_status stg_mrhs_tuning(const stg_gauge *g, stg_prec prec, int nrhs, int *rhs
         set_error("stg_mrhs_tuning: not tuned yet for this lattice, precision and nrhs");
         return STG_ERR_INVALID_ARG;
     }
-    if (shape >= kMspFirst) {
+    if (shape >= kRiFirst) {
+        *rhs_block = ms_ri_nb(shape - kRiFirst);
+        *threads_per_site = -2;  // staged, FP32 on (re, im) FP32x2 pairs
+    } else if (shape >= kMspFirst) {
         *rhs_block = shape == kMspFirst ? 2 : 4;
         *threads_per_site = -1;  // staged, two sites per thread (FX16 / 12-real)
     } else if (shape >= kMrhsShapes) {

@@ -340,10 +340,88 @@ __device__ __forceinline__ void adj_mul_sub2(const Mat3<float> &u, const float2 
         }
 }
 
+// FP32 fields on FP32x2 arithmetic without moving a field value: the real
+// and imaginary part of each colour already sit in the two halves of one
+// float2 of the field record, so every entry of U enters as two broadcast
+// products, A += (Re U) v and B += (Im U) v, and the complex result is
+// Re = A.x - B.y, Im = A.y + B.x.  Two FP32x2 instructions per complex
+// multiply-add in place of four FMAs; each broadcast of U serves the NB
+// systems of the register block (q innermost).
+template <int NB>
+__device__ __forceinline__ void mul_add_ri(const Mat3<float> &u, const float2 (*v)[3], float2 (*A)[3],
+                                           float2 (*B)[3])
+{
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const float2 ur = bc2(u.r[a][b]), ui = bc2(u.i[a][b]);
+#pragma unroll
+            for (int q = 0; q < NB; ++q) {
+                A[q][a] = __ffma2_rn(ur, v[q][b], A[q][a]);
+                B[q][a] = __ffma2_rn(ui, v[q][b], B[q][a]);
+            }
+        }
+}
+
+// acc -= U^dag v: -conj(U_ba) v_b = -(Re U_ba) v_b + i (Im U_ba) v_b enters as
+// A += (-Re U_ba) v_b and B += (Im U_ba) v_b
+template <int NB>
+__device__ __forceinline__ void adj_mul_sub_ri(const Mat3<float> &u, const float2 (*v)[3], float2 (*A)[3],
+                                               float2 (*B)[3])
+{
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const float2 ur = bc2(-u.r[b][a]), ui = bc2(u.i[b][a]);
+#pragma unroll
+            for (int q = 0; q < NB; ++q) {
+                A[q][a] = __ffma2_rn(ur, v[q][b], A[q][a]);
+                B[q][a] = __ffma2_rn(ui, v[q][b], B[q][a]);
+            }
+        }
+}
+
+// RI: a link of the stage with row 2 taken from the tile's rebuilt rows
+// (sign included), so that all three rows enter the mat-vec alike
+__device__ __forceinline__ Mat3<float> ms_link_ri(const char *blk, const float4 *r4, const float2 *r2, int a)
+{
+    const float4 *p = reinterpret_cast<const float4 *>(blk);
+    Mat3<float> u;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const float4 v = p[k * kMTile + a];
+        set_entry(u, 2 * k, v.x, v.y);
+        set_entry(u, 2 * k + 1, v.z, v.w);
+    }
+    const float4 v = p[2 * kMTile + a];
+    set_entry(u, 4, v.x, v.y);
+    set_entry(u, 5, v.z, v.w);
+    const float4 x = r4[a];
+    const float2 y = r2[a];
+    set_entry(u, 6, x.x, x.y);
+    set_entry(u, 7, x.z, x.w);
+    set_entry(u, 8, y.x, y.y);
+    return u;
+}
+
+// the FP32 colour vector of site j as three (re, im) pairs
+__device__ __forceinline__ void load_ri(const char *f, int vh, int j, float2 *v)
+{
+    const float4 *p4 = reinterpret_cast<const float4 *>(f);
+    const float4 x = __ldg(p4 + j);
+    v[0] = make_float2(x.x, x.y);
+    v[1] = make_float2(x.z, x.w);
+    v[2] = __ldg(reinterpret_cast<const float2 *>(p4 + vh) + j);
+}
+
 template <int P>
 __host__ __device__ constexpr unsigned ms_stage_bytes() { return kMTile * 8 * MsLink<P>::kRec; }
 
-template <int P, int NB, int EPI>
+// RI (FP32 only): the mat-vecs on FP32x2 pairs of real and imaginary parts
+// (mul_add_ri); otherwise scalar FMAs for FP32 and system pairs for FX16
+template <int P, int NB, int EPI, bool RI = false>
 __global__ void __launch_bounds__(kMsThreads, STG_MS_MINBLOCKS) k_dslash_ms(const MrhsArgs a)
 {
     typedef float T;
@@ -354,6 +432,11 @@ __global__ void __launch_bounds__(kMsThreads, STG_MS_MINBLOCKS) k_dslash_ms(cons
     __shared__ unsigned done_warps[kMsStages], issued[kMsStages];
     __shared__ int abort_flag;
     __shared__ FF sysw[kMsWarps][kMaxRhs];  // EPI_A_CG: per-warp d^dag q per list slot
+    // RI: row 2 of the tile's eight links per site, rebuilt once per tile
+    // (not once per register block of systems) with the link's sign
+    __shared__ float4 row2s4[RI ? 8 * kMTile : 1];
+    __shared__ float2 row2s2[RI ? 8 * kMTile : 1];
+    static_assert(!RI || kMsGroups == 4, "RI: site group g rebuilds the links of direction g");
     const int vh = a.g.Vh;
     const int ntiles = (vh + kMTile - 1) / kMTile;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -395,20 +478,42 @@ __global__ void __launch_bounds__(kMsThreads, STG_MS_MINBLOCKS) k_dslash_ms(cons
         const int iv = ok ? i : vh - 1;  // past Vh: a valid site's fields, zero links, unstored
         int jf[4], jb[4];
         T s2f[4], s2b[4];
+        T sgf = T(1), sgb = T(1);  // RI: the signs of direction grp at this site
         {
             const Site s = site_of(a.g, iv, a.parity);
 #pragma unroll
             for (int mu = 0; mu < 4; ++mu) {
                 neighbours(a.g, s, iv, mu, jf[mu], jb[mu]);
+                if constexpr (!RI) {
+                    float sf, sb;
+                    link_signs(a.g, s, mu, sf, sb);
+                    s2f[mu] = T(sf * LinkPost<P>::row2);
+                    s2b[mu] = T(sb * LinkPost<P>::row2);
+                }
+            }
+            if constexpr (RI) {
                 float sf, sb;
-                link_signs(a.g, s, mu, sf, sb);
-                s2f[mu] = T(sf * LinkPost<P>::row2);
-                s2b[mu] = T(sb * LinkPost<P>::row2);
+                link_signs(a.g, s, grp, sf, sb);
+                sgf = sf;
+                sgb = sb;
             }
         }
         const bool ready = mbar_wait(smem_addr(&full[st]), par, abort, &g_ms_wait_timeouts);
         if (!__syncthreads_and(ready)) break;  // uniform over the CTA
         const char *sb = stage + (size_t)st * SB;
+        if constexpr (RI) {
+            // every thread rebuilds the forward and backward link of its site
+            // in direction grp; the previous tile's readers have all passed
+            // the barrier above
+#pragma unroll
+            for (int dir = 0; dir < 2; ++dir) {
+                const int l = 2 * grp + dir;
+                const Mat3<T> u = MsLink<P>::load(sb + (size_t)l * LB, site, dir ? sgb : sgf);
+                row2s4[l * kMTile + site] = make_float4(u.r[2][0], u.i[2][0], u.r[2][1], u.i[2][1]);
+                row2s2[l * kMTile + site] = make_float2(u.r[2][2], u.i[2][2]);
+            }
+            __syncthreads();
+        }
 
         for (int k0 = 0; k0 < per; k0 += NB) {
             int rid[NB];
@@ -473,9 +578,39 @@ __global__ void __launch_bounds__(kMsThreads, STG_MS_MINBLOCKS) k_dslash_ms(cons
                         acc[2 * p2 + 1].r[c] = ar[p2][c].y;
                         acc[2 * p2 + 1].i[c] = ai[p2][c].y;
                     }
+            } else if constexpr (RI) {
+                static_assert(P == P32, "RI pairs are FP32 field pairs");
+                float2 A[NB][3], B[NB][3];
+#pragma unroll
+                for (int q = 0; q < NB; ++q)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) A[q][c] = B[q][c] = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int mu = 0; mu < 4; ++mu) {
+                    // one direction's fields at a time (the accumulators
+                    // take twice the registers of the scalar form)
+                    float2 v[NB][3];
+#pragma unroll
+                    for (int q = 0; q < NB; ++q) load_ri(a.in + rid[q] * a.fstride, vh, jf[mu], v[q]);
+                    const Mat3<T> uf = ms_link_ri(sb + (size_t)(2 * mu) * LB, row2s4 + 2 * mu * kMTile,
+                                                  row2s2 + 2 * mu * kMTile, site);
+                    mul_add_ri<NB>(uf, v, A, B);
+#pragma unroll
+                    for (int q = 0; q < NB; ++q) load_ri(a.in + rid[q] * a.fstride, vh, jb[mu], v[q]);
+                    const Mat3<T> ub = ms_link_ri(sb + (size_t)(2 * mu + 1) * LB, row2s4 + (2 * mu + 1) * kMTile,
+                                                  row2s2 + (2 * mu + 1) * kMTile, site);
+                    adj_mul_sub_ri<NB>(ub, v, A, B);
+                }
+#pragma unroll
+                for (int q = 0; q < NB; ++q)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        acc[q].r[c] = A[q][c].x - B[q][c].y;
+                        acc[q].i[c] = A[q][c].y + B[q][c].x;
+                    }
             } else {
-                // FP32: scalar FMAs (packing the fields would cost more moves
-                // than it saves)
+                // FP32: scalar FMAs (packing the fields of two systems would
+                // cost more moves than it saves; RI avoids the moves)
 #pragma unroll
                 for (int q = 0; q < NB; ++q)
 #pragma unroll
@@ -619,22 +754,22 @@ __global__ void __launch_bounds__(kMsThreads, STG_MS_MINBLOCKS) k_dslash_ms(cons
 constexpr int kMrhsStagedShapes = 3;
 __host__ __device__ constexpr int ms_nb(int k) { return k == 0 ? 2 : k == 1 ? 4 : 8; }
 
-template <int P, int NB>
+template <int P, int NB, bool RI = false>
 void launch_ms_nb(int epi, const MrhsArgs &a, cudaStream_t s)
 {
     constexpr unsigned smem = kMsStages * ms_stage_bytes<P>();
     // set once per instantiation (thread-safe static initialisation):
     // resident CTAs on the whole GPU
     static const int resident = [] {
-        cudaFuncSetAttribute(k_dslash_ms<P, NB, EPI_NONE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        cudaFuncSetAttribute(k_dslash_ms<P, NB, EPI_A>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        cudaFuncSetAttribute(k_dslash_ms<P, NB, EPI_GATE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        cudaFuncSetAttribute(k_dslash_ms<P, NB, EPI_A_CG>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(k_dslash_ms<P, NB, EPI_NONE, RI>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(k_dslash_ms<P, NB, EPI_A, RI>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(k_dslash_ms<P, NB, EPI_GATE, RI>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(k_dslash_ms<P, NB, EPI_A_CG, RI>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
             sms = 148;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dslash_ms<P, NB, EPI_A_CG>, kMsThreads,
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dslash_ms<P, NB, EPI_A_CG, RI>, kMsThreads,
                                                           smem) != cudaSuccess || per_sm < 1)
             per_sm = 1;
         return sms * per_sm;
@@ -644,10 +779,10 @@ void launch_ms_nb(int epi, const MrhsArgs &a, cudaStream_t s)
     if (a.grid_limit > 0 && a.grid_limit < cap) cap = a.grid_limit;
     const int grid = ntiles < cap ? ntiles : cap;
     switch (epi) {
-    case EPI_NONE: k_dslash_ms<P, NB, EPI_NONE><<<grid, kMsThreads, smem, s>>>(a); break;
-    case EPI_A: k_dslash_ms<P, NB, EPI_A><<<grid, kMsThreads, smem, s>>>(a); break;
-    case EPI_GATE: k_dslash_ms<P, NB, EPI_GATE><<<grid, kMsThreads, smem, s>>>(a); break;
-    case EPI_A_CG: k_dslash_ms<P, NB, EPI_A_CG><<<grid, kMsThreads, smem, s>>>(a); break;
+    case EPI_NONE: k_dslash_ms<P, NB, EPI_NONE, RI><<<grid, kMsThreads, smem, s>>>(a); break;
+    case EPI_A: k_dslash_ms<P, NB, EPI_A, RI><<<grid, kMsThreads, smem, s>>>(a); break;
+    case EPI_GATE: k_dslash_ms<P, NB, EPI_GATE, RI><<<grid, kMsThreads, smem, s>>>(a); break;
+    case EPI_A_CG: k_dslash_ms<P, NB, EPI_A_CG, RI><<<grid, kMsThreads, smem, s>>>(a); break;
     }
 }
 
@@ -659,8 +794,22 @@ void launch_ms(int k, int epi, const MrhsArgs &a, cudaStream_t s)
     else launch_ms_nb<P, 8>(epi, a, s);
 }
 
+// FP32 staged kernel on (re, im) FP32x2 pairs: NB = 2, 4; its shapes follow
+// the register-fed ones, the staged ones and the two of the FX16 staged
+// kernel with two sites per thread (mrhs_paired.cuh)
+constexpr int kMspShapes = 2;
+constexpr int kMsRiShapes = 2;
+__host__ __device__ constexpr int ms_ri_nb(int k) { return k == 0 ? 2 : 4; }
+
+inline void launch_ms_ri(int k, int epi, const MrhsArgs &a, cudaStream_t s)
+{
+    if (k == 0) launch_ms_nb<P32, 2, true>(epi, a, s);
+    else launch_ms_nb<P32, 4, true>(epi, a, s);
+}
+
 // (NB, TPS) shapes the autotuner chooses from
 constexpr int kMrhsShapes = 9;
+constexpr int kMsRiFirst = kMrhsShapes + kMrhsStagedShapes + kMspShapes;
 __host__ __device__ constexpr int mrhs_nb(int k)
 {
     return k == 0 ? 1 : k == 1 ? 2 : k == 2 ? 4 : k == 3 ? 2 : k == 4 ? 1 : k == 5 ? 2 : k == 6 ? 1 : k == 7 ? 2 : 1;

@@ -30,7 +30,7 @@ namespace stg {
 constexpr int kMspThreads = 128;
 constexpr int kMspWarps = kMspThreads / 32;  // system groups
 constexpr int kMspStages = STG_MSP_STAGES;
-constexpr int kMspShapes = 2;                // NB = 2, 4
+// kMspShapes (mrhs_kernels.cuh): NB = 2, 4
 __host__ __device__ constexpr int msp_nb(int k) { return k == 0 ? 2 : 4; }
 
 static __device__ unsigned g_msp_wait_timeouts;

@@ -300,37 +300,25 @@ def test_bf16_error_is_reported_beside_fp16():
     assert err[stg.STG_FP16] < 2e-3 and err[stg.STG_FP16] < err[stg.STG_BF16] < 1e-2
 
 
-@pytest.mark.parametrize("mass", [1.0, 0.05])
-def test_cg_bf16_inner(mass):
-    """BF16 inner iterations.  At m = 1 (condition number ~65) the solve
-    converges to 1e-10.  At light masses the 8-bit significand of the stored
-    vectors (Dslash error 2e-3, times the condition number 25600 at m = 0.05)
-    cannot drive the true residual down -- measured: at m = 0.3 the solver
-    stops at maxiter -- and the solver then returns a breakdown or
-    not-converged status, never a wrong x."""
+@pytest.mark.parametrize("mass", [1.0, 0.3, 0.05])
+@pytest.mark.parametrize("policy", [stg.STG_CG_RELIABLE, stg.STG_CG_REFINE])
+def test_cg_bf16_inner(mass, policy):
+    """BF16 inner iterations (8-bit significand, Dslash error ~2e-3) reach a
+    1e-10 true residual with reliable updates at delta = 0.1, with the Eq. 6
+    start and with Fig. 2's restart, down to m = 0.05 on 8^4 (measured on
+    GB300: 133 / 144 iterations with 10 updates at m = 0.05).  The solution
+    is checked against the oracle's A."""
     dims, tol = (8, 8, 8, 8), 1e-10
     U = gen.gauge_field(dims, "exp", seed=11, eps=0.4)
     b = gen.source(dims, seed=12)
     with Gauge(dims, U, sloppy=stg.STG_BF16, recon=12) as g:
         bd = _to_dev(b)
         x = torch.zeros_like(bd)
-        try:
-            st = stg.stg_cg_solve(g.handle, bd, x, mass, tol, g.params(maxiter=20000))
-        except stg.StgError as e:
-            # only the light mass may fail, and it must say so truthfully:
-            # a breakdown or maxiter status, stats filled, and for maxiter the
-            # reported true residual is the oracle's residual of the x written
-            assert mass < 1.0 and e.status in (stg.STG_ERR_BREAKDOWN, stg.STG_ERR_NOT_CONVERGED)
-            st = e.stats
-            assert st["iters"] > 0 and st["true_res"] > tol
-            if e.status == stg.STG_ERR_NOT_CONVERGED:
-                r = b - oracle.apply_A(dims, U, mass, x.cpu().numpy())
-                tr = np.linalg.norm(r) / np.linalg.norm(b)
-                assert abs(tr - st["true_res"]) <= 1e-6 * tr
-            return
-    assert mass == 1.0 or st["true_res"] <= tol
+        st = stg.stg_cg_solve(g.handle, bd, x, mass, tol,
+                              g.params(policy=policy, delta=0.1, maxiter=20000))
+    assert st["true_res"] <= tol
     _check_solution(dims, U, mass, b, x.cpu().numpy(), tol)
-    assert st["sloppy_iters"] == st["iters"] > 0
+    assert 0 < st["updates"] and st["sloppy_iters"] >= 0.9 * st["iters"] > 0
 
 
 def test_dependent_launch_changes_no_bit():
