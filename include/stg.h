@@ -382,11 +382,13 @@ size_t stg_lgroup_bytes(int max_systems, long max_vh, stg_prec sloppy);
  * threads_per_site = 0 names the staged kernel (12-real FP32 / FX16 links
  * streamed through shared memory, one link load per site for all systems,
  * NB systems per thread and pass), threads_per_site = -1 its FX16 / 12-real
- * form with two sites per thread on packed FP32x2 arithmetic.
+ * form with two sites per thread on packed FP32x2 arithmetic,
+ * threads_per_site = -2 its FP32 / 12-real form with the real and imaginary
+ * part of each colour in the halves of FP32x2 registers.
  * STG_ERR_INVALID_ARG if not tuned yet.  The environment variable
  * STG_MRHS_SHAPE=<k> forces shape k (0-8: register-fed (NB, TPS); 9-11:
- * staged NB = 2, 4, 8; 12-13: staged two sites per thread, NB = 2, 4) where
- * it applies. */
+ * staged NB = 2, 4, 8; 12-13: staged two sites per thread, NB = 2, 4;
+ * 14-15: staged on (re, im) FP32x2 pairs, NB = 2, 4) where it applies. */
 stg_status stg_mrhs_tuning(const stg_gauge *g, stg_prec prec, int nrhs, int *rhs_block,
                            int *threads_per_site);
 
