@@ -383,8 +383,9 @@ size_t stg_lgroup_bytes(int max_systems, long max_vh, stg_prec sloppy);
  * streamed through shared memory, one link load per site for all systems,
  * NB systems per thread and pass), threads_per_site = -1 its FX16 / 12-real
  * form with two sites per thread on packed FP32x2 arithmetic,
- * threads_per_site = -2 its FP32 / 12-real form with the real and imaginary
- * part of each colour in the halves of FP32x2 registers.
+ * threads_per_site = -2 its form with the real and imaginary part of each
+ * colour in the halves of FP32x2 registers and each tile's links rebuilt
+ * once in shared memory (12-real FP32 and FX16).
  * STG_ERR_INVALID_ARG if not tuned yet.  The environment variable
  * STG_MRHS_SHAPE=<k> forces shape k (0-8: register-fed (NB, TPS); 9-11:
  * staged NB = 2, 4, 8; 12-13: staged two sites per thread, NB = 2, 4;

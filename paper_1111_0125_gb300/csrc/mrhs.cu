@@ -52,8 +52,8 @@ static bool same_key(const TuneEntry &e, const int *dims, int prec, int recon, i
 // shapes 0 .. kMrhsShapes - 1: register-fed (NB, TPS); then the staged
 // kernel with NB = ms_nb(shape - kMrhsShapes) (12-real FP32 / FX16 links);
 // then (FX16 / 12-real only) the staged kernel with two sites per thread,
-// NB = msp_nb(shape - kMrhsShapes - kMrhsStagedShapes); then (FP32 / 12-real
-// only) the staged kernel on (re, im) FP32x2 pairs, NB = ms_ri_nb(shape -
+// NB = msp_nb(shape - kMrhsShapes - kMrhsStagedShapes); then (12-real FP32
+// or FX16) the staged kernel on (re, im) FP32x2 pairs, NB = ms_ri_nb(shape -
 // kRiFirst)
 constexpr int kMspFirst = kMrhsShapes + kMrhsStagedShapes;
 constexpr int kMspCount = kMspShapes;  // NB = 2, 4 (mrhs_paired.cuh)
@@ -71,7 +71,7 @@ static bool shape_ok(const LinkField *lf, int shape)
     if (shape < kMrhsShapes) return true;
     if (shape < kMspFirst) return staged_ok(lf);
     if (shape < kRiFirst) return staged_ok(lf) && lf->prec == PX16;
-    return staged_ok(lf) && lf->prec == P32;
+    return staged_ok(lf);
 }
 
 static void tune_load_file_locked()
@@ -147,7 +147,7 @@ static stg_status launch_m(const stg_gauge *g, const LinkField *lf, int shape, i
     if (shape >= kMrhsShapes) {
         if (!shape_ok(lf, shape)) {
             set_error("multi-system Dslash: the staged kernel needs the tile-major 12-real links "
-                      "(FP32 or FX16; two sites per thread: FX16; (re, im) pairs: FP32)");
+                      "(FP32 or FX16; two sites per thread: FX16)");
             return STG_ERR_UNSUPPORTED;
         }
         a.lt = lf->mtiled + (size_t)a.parity * lf->mtiled_parity_bytes;
@@ -927,7 +927,7 @@ stg_status stg_mrhs_tuning(const stg_gauge *g, stg_prec prec, int nrhs, int *rhs
     }
     if (shape >= kRiFirst) {
         *rhs_block = ms_ri_nb(shape - kRiFirst);
-        *threads_per_site = -2;  // staged, FP32 on (re, im) FP32x2 pairs
+        *threads_per_site = -2;  // staged, on (re, im) FP32x2 pairs
     } else if (shape >= kMspFirst) {
         *rhs_block = shape == kMspFirst ? 2 : 4;
         *threads_per_site = -1;  // staged, two sites per thread (FX16 / 12-real)

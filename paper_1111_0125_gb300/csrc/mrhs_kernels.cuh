@@ -264,6 +264,7 @@ __global__ void __launch_bounds__(kMrhsBlock) k_dslash_m(const MrhsArgs a)
 #ifndef STG_MS_MINBLOCKS
 #define STG_MS_MINBLOCKS 2
 #endif
+
 constexpr int kMsThreads = STG_MS_THREADS;
 constexpr int kMsGroups = kMsThreads / kMTile;
 constexpr int kMsWarps = kMsThreads / 32;
@@ -406,6 +407,46 @@ __device__ __forceinline__ Mat3<float> ms_link_ri(const char *blk, const float4 
     return u;
 }
 
+// RI, FX16: a link decoded once per tile into FP32 (true values, row 2
+// rebuilt with its sign) as four float4 planes and one float2 plane
+__device__ __forceinline__ Mat3<float> ms_link_fx(const float4 *x4, const float2 *x2, int a)
+{
+    Mat3<float> u;
+    const float4 p0 = x4[a], p1 = x4[kMTile + a], p2 = x4[2 * kMTile + a], p3 = x4[3 * kMTile + a];
+    const float2 p4 = x2[a];
+    set_entry(u, 0, p0.x, p0.y);
+    set_entry(u, 1, p0.z, p0.w);
+    set_entry(u, 2, p1.x, p1.y);
+    set_entry(u, 3, p1.z, p1.w);
+    set_entry(u, 4, p2.x, p2.y);
+    set_entry(u, 5, p2.z, p2.w);
+    set_entry(u, 6, p3.x, p3.y);
+    set_entry(u, 7, p3.z, p3.w);
+    set_entry(u, 8, p4.x, p4.y);
+    return u;
+}
+
+// one FX16 (re, im) word as an FP32 pair: the biased values K + q from two
+// byte permutes, then (K + q) s - K s in one FP32x2 FMA (K s is exact for
+// the 15-bit scale, so this rounds once, like q s)
+__device__ __forceinline__ float2 fx_pair(unsigned w, float2 s2, float2 ks2)
+{
+    const float2 b = make_float2(__int_as_float((int)__byte_perm(w, 0x4B40u, 0x5410)),
+                                 __int_as_float((int)__byte_perm(w, 0x4B40u, 0x5432)));
+    return __ffma2_rn(b, s2, ks2);
+}
+
+// the FX16 colour vector of site j as three (re, im) pairs
+__device__ __forceinline__ void load_ri_fx(const char *f, int j, float2 *v)
+{
+    const uint4 u = __ldg(reinterpret_cast<const uint4 *>(f) + j);
+    const float sc = __uint_as_float(u.w);
+    const float2 s2 = bc2(sc), ks2 = bc2(-12615680.0f * sc);
+    v[0] = fx_pair(u.x, s2, ks2);
+    v[1] = fx_pair(u.y, s2, ks2);
+    v[2] = fx_pair(u.z, s2, ks2);
+}
+
 // the FP32 colour vector of site j as three (re, im) pairs
 __device__ __forceinline__ void load_ri(const char *f, int vh, int j, float2 *v)
 {
@@ -419,8 +460,9 @@ __device__ __forceinline__ void load_ri(const char *f, int vh, int j, float2 *v)
 template <int P>
 __host__ __device__ constexpr unsigned ms_stage_bytes() { return kMTile * 8 * MsLink<P>::kRec; }
 
-// RI (FP32 only): the mat-vecs on FP32x2 pairs of real and imaginary parts
-// (mul_add_ri); otherwise scalar FMAs for FP32 and system pairs for FX16
+// RI: the mat-vecs on FP32x2 pairs of real and imaginary parts (mul_add_ri),
+// with the links' row 2 (FP32) or whole links (FX16) rebuilt once per tile in
+// shared memory; otherwise scalar FMAs for FP32 and system pairs for FX16
 template <int P, int NB, int EPI, bool RI = false>
 __global__ void __launch_bounds__(kMsThreads, STG_MS_MINBLOCKS) k_dslash_ms(const MrhsArgs a)
 {
@@ -434,8 +476,13 @@ __global__ void __launch_bounds__(kMsThreads, STG_MS_MINBLOCKS) k_dslash_ms(cons
     __shared__ FF sysw[kMsWarps][kMaxRhs];  // EPI_A_CG: per-warp d^dag q per list slot
     // RI: row 2 of the tile's eight links per site, rebuilt once per tile
     // (not once per register block of systems) with the link's sign
-    __shared__ float4 row2s4[RI ? 8 * kMTile : 1];
-    __shared__ float2 row2s2[RI ? 8 * kMTile : 1];
+    // (FP32), or the whole FP32 links (FX16: decoded once per tile)
+    constexpr int kR2 = (RI && P == P32) ? 8 * kMTile : 1;
+    constexpr int kLX = (RI && P == PX16) ? 8 * kMTile : 1;
+    __shared__ float4 row2s4[kR2];
+    __shared__ float2 row2s2[kR2];
+    __shared__ float4 lkx4[4 * kLX];
+    __shared__ float2 lkx2[kLX];
     static_assert(!RI || kMsGroups == 4, "RI: site group g rebuilds the links of direction g");
     const int vh = a.g.Vh;
     const int ntiles = (vh + kMTile - 1) / kMTile;
@@ -508,9 +555,24 @@ __global__ void __launch_bounds__(kMsThreads, STG_MS_MINBLOCKS) k_dslash_ms(cons
 #pragma unroll
             for (int dir = 0; dir < 2; ++dir) {
                 const int l = 2 * grp + dir;
-                const Mat3<T> u = MsLink<P>::load(sb + (size_t)l * LB, site, dir ? sgb : sgf);
-                row2s4[l * kMTile + site] = make_float4(u.r[2][0], u.i[2][0], u.r[2][1], u.i[2][1]);
-                row2s2[l * kMTile + site] = make_float2(u.r[2][2], u.i[2][2]);
+                const T sg = dir ? sgb : sgf;
+                if constexpr (P == P32) {
+                    const Mat3<T> u = MsLink<P>::load(sb + (size_t)l * LB, site, sg);
+                    row2s4[l * kMTile + site] = make_float4(u.r[2][0], u.i[2][0], u.r[2][1], u.i[2][1]);
+                    row2s2[l * kMTile + site] = make_float2(u.r[2][2], u.i[2][2]);
+                } else {
+                    // stored entries are q = 32767 U; row 2 from them carries
+                    // 32767^2, so it takes the sign times 1/32767, then every
+                    // entry takes 1/32767
+                    Mat3<T> u = MsLink<P>::load(sb + (size_t)l * LB, site, sg * T(LinkPost<P>::row2));
+                    constexpr T k = T(LinkPost<P>::k);
+                    float4 *x4 = lkx4 + 4 * l * kMTile + site;
+                    x4[0] = make_float4(k * u.r[0][0], k * u.i[0][0], k * u.r[0][1], k * u.i[0][1]);
+                    x4[kMTile] = make_float4(k * u.r[0][2], k * u.i[0][2], k * u.r[1][0], k * u.i[1][0]);
+                    x4[2 * kMTile] = make_float4(k * u.r[1][1], k * u.i[1][1], k * u.r[1][2], k * u.i[1][2]);
+                    x4[3 * kMTile] = make_float4(k * u.r[2][0], k * u.i[2][0], k * u.r[2][1], k * u.i[2][1]);
+                    lkx2[l * kMTile + site] = make_float2(k * u.r[2][2], k * u.i[2][2]);
+                }
             }
             __syncthreads();
         }
@@ -529,7 +591,7 @@ __global__ void __launch_bounds__(kMsThreads, STG_MS_MINBLOCKS) k_dslash_ms(cons
             Vec3<T> acc[NB];
             // no branches in the hot loop: a slot that is not running reads
             // system rid = 0 (valid memory) and its result is dropped below
-            if constexpr (P == PX16) {
+            if constexpr (P == PX16 && !RI) {
                 // systems 2p and 2p + 1 share float2 accumulators: the decode
                 // of the 16-bit fields leaves the FMA pipe the busier one
                 float2 ar[NB / 2][3], ai[NB / 2][3];
@@ -579,7 +641,6 @@ __global__ void __launch_bounds__(kMsThreads, STG_MS_MINBLOCKS) k_dslash_ms(cons
                         acc[2 * p2 + 1].i[c] = ai[p2][c].y;
                     }
             } else if constexpr (RI) {
-                static_assert(P == P32, "RI pairs are FP32 field pairs");
                 float2 A[NB][3], B[NB][3];
 #pragma unroll
                 for (int q = 0; q < NB; ++q)
@@ -591,14 +652,23 @@ __global__ void __launch_bounds__(kMsThreads, STG_MS_MINBLOCKS) k_dslash_ms(cons
                     // take twice the registers of the scalar form)
                     float2 v[NB][3];
 #pragma unroll
-                    for (int q = 0; q < NB; ++q) load_ri(a.in + rid[q] * a.fstride, vh, jf[mu], v[q]);
-                    const Mat3<T> uf = ms_link_ri(sb + (size_t)(2 * mu) * LB, row2s4 + 2 * mu * kMTile,
-                                                  row2s2 + 2 * mu * kMTile, site);
+                    for (int q = 0; q < NB; ++q) {
+                        if constexpr (P == P32) load_ri(a.in + rid[q] * a.fstride, vh, jf[mu], v[q]);
+                        else load_ri_fx(a.in + rid[q] * a.fstride, jf[mu], v[q]);
+                    }
+                    const Mat3<T> uf = (P == P32)
+                        ? ms_link_ri(sb + (size_t)(2 * mu) * LB, row2s4 + 2 * mu * kMTile, row2s2 + 2 * mu * kMTile, site)
+                        : ms_link_fx(lkx4 + 4 * (2 * mu) * kMTile, lkx2 + (2 * mu) * kMTile, site);
                     mul_add_ri<NB>(uf, v, A, B);
 #pragma unroll
-                    for (int q = 0; q < NB; ++q) load_ri(a.in + rid[q] * a.fstride, vh, jb[mu], v[q]);
-                    const Mat3<T> ub = ms_link_ri(sb + (size_t)(2 * mu + 1) * LB, row2s4 + (2 * mu + 1) * kMTile,
-                                                  row2s2 + (2 * mu + 1) * kMTile, site);
+                    for (int q = 0; q < NB; ++q) {
+                        if constexpr (P == P32) load_ri(a.in + rid[q] * a.fstride, vh, jb[mu], v[q]);
+                        else load_ri_fx(a.in + rid[q] * a.fstride, jb[mu], v[q]);
+                    }
+                    const Mat3<T> ub = (P == P32)
+                        ? ms_link_ri(sb + (size_t)(2 * mu + 1) * LB, row2s4 + (2 * mu + 1) * kMTile,
+                                     row2s2 + (2 * mu + 1) * kMTile, site)
+                        : ms_link_fx(lkx4 + 4 * (2 * mu + 1) * kMTile, lkx2 + (2 * mu + 1) * kMTile, site);
                     adj_mul_sub_ri<NB>(ub, v, A, B);
                 }
 #pragma unroll
@@ -636,7 +706,7 @@ __global__ void __launch_bounds__(kMsThreads, STG_MS_MINBLOCKS) k_dslash_ms(cons
             for (int q = 0; q < NB; ++q) {
                 dot[q].hi = dot[q].lo = 0.f;
                 if (!ok || !run[q]) continue;
-                if (P == PX16) {
+                if (P == PX16 && !RI) {  // RI: the links carry 1/32767 already
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
                         acc[q].r[c] *= T(LinkPost<PX16>::k);
@@ -794,17 +864,18 @@ void launch_ms(int k, int epi, const MrhsArgs &a, cudaStream_t s)
     else launch_ms_nb<P, 8>(epi, a, s);
 }
 
-// FP32 staged kernel on (re, im) FP32x2 pairs: NB = 2, 4; its shapes follow
+// staged kernel on (re, im) FP32x2 pairs (FP32 and FX16): NB = 2, 4; its shapes follow
 // the register-fed ones, the staged ones and the two of the FX16 staged
 // kernel with two sites per thread (mrhs_paired.cuh)
 constexpr int kMspShapes = 2;
 constexpr int kMsRiShapes = 2;
 __host__ __device__ constexpr int ms_ri_nb(int k) { return k == 0 ? 2 : 4; }
 
-inline void launch_ms_ri(int k, int epi, const MrhsArgs &a, cudaStream_t s)
+template <int P>
+void launch_ms_ri(int k, int epi, const MrhsArgs &a, cudaStream_t s)
 {
-    if (k == 0) launch_ms_nb<P32, 2, true>(epi, a, s);
-    else launch_ms_nb<P32, 4, true>(epi, a, s);
+    if (k == 0) launch_ms_nb<P, 2, true>(epi, a, s);
+    else launch_ms_nb<P, 4, true>(epi, a, s);
 }
 
 // (NB, TPS) shapes the autotuner chooses from

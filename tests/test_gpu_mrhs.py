@@ -62,8 +62,8 @@ def test_dslash_mrhs_matches_oracle_and_single(dims, prec, recon, n):
             assert recon == 12 and nb in (2, 4, 8)
         elif tps == -1:  # staged, two sites per thread (FX16 / 12-real only)
             assert prec == stg.STG_FX16 and recon == 12 and nb in (2, 4)
-        elif tps == -2:  # staged on (re, im) FP32x2 pairs (FP32 / 12-real only)
-            assert prec == stg.STG_FP32 and recon == 12 and nb in (2, 4)
+        elif tps == -2:  # staged on (re, im) FP32x2 pairs (12-real only)
+            assert recon == 12 and nb in (2, 4)
         else:
             assert nb in (1, 2, 4) and tps in (1, 2, 4, 8, 16) and tps <= max(1, n)
 
@@ -85,16 +85,17 @@ def test_apply_A_mrhs_per_system_masses(prec):
 
 
 @pytest.mark.parametrize("prec,shape,nb", [(p, s, nb) for p in (stg.STG_FP32, stg.STG_FX16)
-                                           for s, nb in (("9", 2), ("10", 4), ("11", 8))]
-                         + [(stg.STG_FP32, "14", 2), (stg.STG_FP32, "15", 4)])
+                                           for s, nb in (("9", 2), ("10", 4), ("11", 8),
+                                                         ("14", 2), ("15", 4))])
 @pytest.mark.parametrize("grid", [None, "2"])
 def test_staged_mrhs_matches_register_fed(monkeypatch, prec, shape, nb, grid):
     """The staged multi-system kernel (links of a 64-site tile in shared
     memory, shared by every system) against the register-fed kernel and the
     oracle, for each register block NB; a grid of 2 CTAs makes each CTA walk
     12 of the 23 tiles (ragged last tile) through its 2-stage ring.  Shapes
-    14 and 15 are its FP32 form on (re, im) FP32x2 pairs, with row 2 of
-    each tile's links rebuilt once into shared memory."""
+    14 and 15 are its form on (re, im) FP32x2 pairs, with each tile's links
+    rebuilt once into shared memory (row 2 for FP32, the decoded FP32 links
+    for FX16)."""
     dims, n = (6, 4, 10, 12), 9
     U = gen.gauge_field(dims, "exp", seed=6, eps=0.5)
     chis = list(gen.source(dims, seed=8, nrhs=n))
@@ -127,20 +128,6 @@ def test_staged_mrhs_matches_register_fed(monkeypatch, prec, shape, nb, grid):
         for k in range(n):
             r = chis[k] - oracle.apply_A(dims, U, masses[k], xs[k])
             assert np.linalg.norm(r) <= 1e-10 * np.linalg.norm(chis[k]), k
-
-
-def test_ri_shapes_are_fp32_only(monkeypatch):
-    """The (re, im) FP32x2 shapes apply to FP32 / 12-real links only: forced
-    on FX16 links the choice falls back to the autotuner."""
-    dims, n = (4, 4, 4, 8), 4
-    U = gen.gauge_field(dims, "exp", seed=6, eps=0.5)
-    chis = list(gen.source(dims, seed=8, nrhs=n))
-    with stg.Gauge(dims, U, sloppy=stg.STG_FX16, recon=12) as g:
-        buf, fb = _pack_batch(g, chis, stg.STG_FX16)
-        monkeypatch.setenv("STG_MRHS_SHAPE", "15")
-        out = torch.empty_like(buf)
-        stg.stg_dslash_mrhs(g.handle, 0, n, buf, out, stg.STG_FX16)
-        assert stg.stg_mrhs_tuning(g.handle, stg.STG_FX16, n)[1] != -2
 
 
 @pytest.mark.parametrize("shape,nb", [("12", 2), ("13", 4)])
