@@ -114,6 +114,8 @@ def parse():
                     help="c5: every session on a default-priority stream")
     ap.add_argument("--sweep", type=float, nargs="*", default=[0.3, 0.5],
                     help="c5: further offered loads (fractions of saturation) to report")
+    ap.add_argument("--check-every", type=int, default=0,
+                    help="c4: CG iterations per chunk of the batched solve (0: the library's 16)")
     ap.add_argument("--nrhs", type=int, default=16)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--no-extras", action="store_true",
@@ -459,6 +461,8 @@ def c4_measure(args, steps, warmup, one_by_one_reps=1):
     p = g.params(policy=stg.STG_CG_RELIABLE, sloppy=sloppy)
     if args.delta is not None and args.workload == "c4":
         p.delta = args.delta
+    if args.check_every > 0:
+        p.check_every = args.check_every
 
     def batched():
         x = torch.zeros_like(src)
@@ -507,6 +511,13 @@ def c4_measure(args, steps, warmup, one_by_one_reps=1):
     s1.record(stream)
     s1.synchronize()
     t_m = s0.elapsed_time(s1) / 20
+    # the fused operator A = m^2 - D_eo D_oe of all n systems (both half-passes)
+    s0.record(stream)
+    for _ in range(10):
+        stg.stg_apply_A_mrhs(g.handle, n, masses, fin, fout, sloppy, stream)
+    s1.record(stream)
+    s1.synchronize()
+    t_a = s0.elapsed_time(s1) / 10
     L, S = LINK_BYTES[(c4_sloppy, args.recon)], FIELD_BYTES[c4_sloppy]
     # links once per NB x TPS systems (register-fed), once for all (staged,
     # tb = 0, or staged with two sites per thread, tb = -1)
@@ -520,7 +531,8 @@ def c4_measure(args, steps, warmup, one_by_one_reps=1):
         "solves_per_s": n / t_batch, "batched_ms": 1000.0 * t_batch, "steps": steps,
         "warmup": warmup, "one_by_one_ms": 1000.0 * t_single,
         "speedup_batched_vs_one_by_one": t_single / t_batch,
-        "sloppy_storage": c4_sloppy, "recon": args.recon,
+        "sloppy_storage": c4_sloppy, "recon": args.recon, "delta": p.delta,
+        "check_every": p.check_every if p.check_every > 0 else 16,
         "masses": [round(float(m), 6) for m in masses],
         "iters": [s_["iters"] for s_ in st], "updates": [s_["updates"] for s_ in st],
         "true_res_max": max(s_["true_res"] for s_ in st),
@@ -530,7 +542,7 @@ def c4_measure(args, steps, warmup, one_by_one_reps=1):
                                    "k_dslash_msp (staged, two sites per thread)" if tb == -1
                                    else "k_dslash_ms (staged, (re, im) FP32x2 pairs)" if tb == -2
                                    else "k_dslash_m"),
-                        "launch_ms": t_m,
+                        "launch_ms": t_m, "apply_A_ms": t_a,
                         "algorithmic_bytes_per_launch": nbytes,
                         "bytes_per_site_per_system": nbytes / vh / n,
                         "achieved": achieved, "peak": peak, "peak_source": src_, "unit": "GB/s",
