@@ -511,6 +511,14 @@ def c4_measure(args, steps, warmup, one_by_one_reps=1):
     s1.record(stream)
     s1.synchronize()
     t_m = s0.elapsed_time(s1) / 20
+    # one system's Dslash alone at this size (the single-right-hand-side kernel)
+    stg.stg_dslash(g.handle, 1, fin[:fb], fout[:fb], sloppy, stream)
+    s0.record(stream)
+    for _ in range(20):
+        stg.stg_dslash(g.handle, 1, fin[:fb], fout[:fb], sloppy, stream)
+    s1.record(stream)
+    s1.synchronize()
+    t_1 = s0.elapsed_time(s1) / 20
     # the fused operator A = m^2 - D_eo D_oe of all n systems (both half-passes)
     s0.record(stream)
     for _ in range(10):
@@ -525,6 +533,7 @@ def c4_measure(args, steps, warmup, one_by_one_reps=1):
     nbytes = vh * (8 * L * link_passes + 2 * S * n)
     peak, src_ = measured_hbm()
     achieved = nbytes / (t_m / 1000.0) / 1e9
+    bytes_1 = vh * (8 * L + 2 * S)
     g.close()
     return {
         "workload": "24^3x48, 16 systems batched, masses log-uniform [0.005, 0.05], tol 1e-10",
@@ -555,6 +564,9 @@ def c4_measure(args, steps, warmup, one_by_one_reps=1):
                                 "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                                 "frac": vh * n * 576 / (t_m / 1000.0) / 1e12 / FP32_PEAK_TFLOPS,
                                 "peak_source": "nominal: SM count x FP32 lanes x 2 x max SM clock"}},
+        "single_dslash": {"launch_ms": t_1, "algorithmic_bytes_per_launch": bytes_1,
+                          "achieved": bytes_1 / (t_1 / 1000.0) / 1e9, "peak": peak,
+                          "unit": "GB/s", "frac": bytes_1 / (t_1 / 1000.0) / 1e9 / peak},
         "clocks": ck,
     }
 

@@ -9,7 +9,10 @@ times.
   size).
 * 16^3 x 32, exp(i 0.4 H), m = 0.01: mixed FP32 CG and plain FP64 CG both
   reach a 1e-10 true residual (oracle's A) and agree within kappa * tol.
-* 24^3 x 48, exp(i 0.5 H): sampled Dslash parity.
+* 24^3 x 48, exp(i 0.5 H): sampled Dslash parity; the 16-system Dslash of
+  the batched workload (sources seed 1 onward, FP32 and FX16 / 12-real) on
+  the autotuner's kernel and on both (re, im) FP32x2 shapes, every system at
+  sampled sites against the oracle.
 """
 import numpy as np
 import pytest
@@ -66,6 +69,32 @@ def test_dslash_sampled_sites(dims, eps, prec, recon):
             sites = _sample_sites(dims, parity, 4096, seed=parity + 3)
             want = oracle.dslash_sites(dims, U, chi_r, parity, sites)
             assert _rel_rows(out[sites], want) < TOL[prec], (prec, recon, parity)
+
+
+@pytest.mark.parametrize("prec", [stg.STG_FP32, stg.STG_FX16])
+@pytest.mark.parametrize("shape", [None, "14", "15"])
+def test_mrhs_dslash_sampled_sites_24x48(monkeypatch, prec, shape):
+    dims, n = (24, 24, 24, 48), 16
+    if shape is not None:
+        monkeypatch.setenv("STG_MRHS_SHAPE", shape)
+    U = _gauge(dims, 0.5)
+    chis = gen.source(dims, seed=1, nrhs=n)
+    with stg.Gauge(dims, U, sloppy=prec, recon=12) as g:
+        fb = stg.stg_field_bytes(g.handle, prec)
+        buf = torch.empty(n * fb, dtype=torch.uint8, device="cuda")
+        for k in range(n):
+            stg.stg_pack_field(g.handle, prec, torch.from_numpy(chis[k]).cuda(), buf[k * fb:(k + 1) * fb])
+        out = torch.empty_like(buf)
+        stg.stg_dslash_mrhs(g.handle, 1, n, buf, out, prec)
+        nb, tps = stg.stg_mrhs_tuning(g.handle, prec, n)
+        if shape is not None:
+            assert (nb, tps) == ({"14": 2, "15": 4}[shape], -2)
+        sites = _sample_sites(dims, 1, 1024, seed=7)
+        for k in range(n):
+            chi_r = g.unpack(buf[k * fb:(k + 1) * fb], prec).cpu().numpy()
+            got = g.unpack(out[k * fb:(k + 1) * fb], prec).cpu().numpy()
+            want = oracle.dslash_sites(dims, U, chi_r, 1, sites)
+            assert _rel_rows(got[sites], want) < TOL[prec], (prec, shape, k)
 
 
 @pytest.mark.parametrize("prec", [stg.STG_FP16, stg.STG_FX16])
