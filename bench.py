@@ -83,7 +83,8 @@ def parse():
     ap.add_argument("--kernels", default="all", choices=["all", "sloppy", "f64"],
                     help="--kernels-only: the sloppy-precision Dslash and A, the FP64 Dslash, "
                          "or both")
-    ap.add_argument("--workload", default="c3", choices=["c3", "c4", "c5", "lgroup", "e1", "slabs"],
+    ap.add_argument("--workload", default="c3",
+                    choices=["c3", "c4", "c5", "lgroup", "e1", "slabs", "oracle"],
                     help="c3: 32^3x64 single solve (default); c4: 24^3x48, 16 systems "
                          "batched; c5: Poisson stream of solve requests (serving); lgroup: "
                          "systems on several small lattices in one lattice-group session "
@@ -1001,8 +1002,57 @@ def run_slabs(args):
         "reps": reps, "dirac": table, "cg": cg}), flush=True)
 
 
+# lattices of the configurations: (name, dims, links, eps)
+ORACLE_LATTICES = [("c1", (4, 4, 4, 4), "haar", 0.0), ("c2", (16, 16, 16, 32), "exp", 0.4),
+                   ("c4", (24, 24, 24, 48), "exp", 0.5), ("c3", (32, 32, 32, 64), "exp", 0.6),
+                   ("e1", (28, 28, 28, 96), "exp", 0.6)]
+
+
+def run_oracle(args):
+    """The FP64 oracle's Dslash and A (as they stand: plain C, OpenMP site
+    loop) on every configuration's lattice, on all host cores and on one
+    core: the median of repeated calls, each measurement about a second, with
+    the compulsory bytes per call (FP64 / 18-real: 1248 B per site for the
+    half-pass, 2544 B for A) over that time.  Host cores only; no GPU."""
+    import gen
+    import oracle
+    oracle.build()
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    rows = []
+    for name, dims, kind, eps in ORACLE_LATTICES:
+        U = gen.gauge_field(dims, kind, seed=0, eps=eps) if kind == "exp" else gen.gauge_field(dims, kind, seed=0)
+        chi = gen.source(dims, seed=1)
+        vh = chi.shape[0]
+        row = {"config": name, "lattice": "x".join(map(str, dims)), "vh": vh}
+        for label, nt in (("all_cores", cores), ("one_core", 1)):
+            with _OmpThreads(nt):
+                for op, fn, bps in (("dslash", lambda: oracle.dslash(dims, U, chi, 1), 1248),
+                                    ("apply_A", lambda: oracle.apply_A(dims, U, 0.01, chi), 2544)):
+                    t0 = time.perf_counter()
+                    fn()
+                    first = time.perf_counter() - t0
+                    reps = max(1, min(50, int(1.0 / max(first, 1e-6))))
+                    ts = []
+                    for _ in range(reps):
+                        t0 = time.perf_counter()
+                        fn()
+                        ts.append(time.perf_counter() - t0)
+                    t = statistics.median(ts)
+                    row[f"{op}_{label}_ms"] = 1000.0 * t
+                    row[f"{op}_{label}_gbs"] = vh * bps / t / 1e9
+                    row[f"{op}_{label}_reps"] = reps
+        rows.append(row)
+        print(json.dumps({"oracle_row": row}), flush=True)
+    print(json.dumps({"workload": "oracle Dslash and A, FP64 / 18-real, host cores", "cores": cores,
+                      "kind": "oracle", "unit": "ms per call (median)", "data": "synthetic",
+                      "rows": rows}), flush=True)
+
+
 def main():
     args = parse()
+    if args.workload == "oracle":
+        run_oracle(args)
+        return
     dims = tuple(int(v) for v in args.lattice.split(","))
     if args.impl == "reference":
         run_reference(args, dims)
