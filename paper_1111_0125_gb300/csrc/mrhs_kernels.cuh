@@ -264,7 +264,6 @@ __global__ void __launch_bounds__(kMrhsBlock) k_dslash_m(const MrhsArgs a)
 #ifndef STG_MS_MINBLOCKS
 #define STG_MS_MINBLOCKS 2
 #endif
-
 constexpr int kMsThreads = STG_MS_THREADS;
 constexpr int kMsGroups = kMsThreads / kMTile;
 constexpr int kMsWarps = kMsThreads / 32;
@@ -341,13 +340,14 @@ __device__ __forceinline__ void adj_mul_sub2(const Mat3<float> &u, const float2 
         }
 }
 
-// FP32 fields on FP32x2 arithmetic without moving a field value: the real
-// and imaginary part of each colour already sit in the two halves of one
-// float2 of the field record, so every entry of U enters as two broadcast
-// products, A += (Re U) v and B += (Im U) v, and the complex result is
-// Re = A.x - B.y, Im = A.y + B.x.  Two FP32x2 instructions per complex
-// multiply-add in place of four FMAs; each broadcast of U serves the NB
-// systems of the register block (q innermost).
+// Colour vectors on FP32x2 arithmetic without moving a field value: the real
+// and imaginary part of each colour sit in the two halves of one float2 (for
+// FP32 as the field record holds them, for FX16 as one decoded word), so
+// every entry of U enters as two broadcast products, A += (Re U) v and
+// B += (Im U) v, and the complex result is Re = A.x - B.y, Im = A.y + B.x.
+// Two FP32x2 instructions per complex multiply-add in place of four FMAs;
+// each broadcast of U serves the NB systems of the register block (q
+// innermost).
 template <int NB>
 __device__ __forceinline__ void mul_add_ri(const Mat3<float> &u, const float2 (*v)[3], float2 (*A)[3],
                                            float2 (*B)[3])
