@@ -116,7 +116,7 @@ def parse():
     ap.add_argument("--sweep", type=float, nargs="*", default=[0.3, 0.5],
                     help="c5: further offered loads (fractions of saturation) to report")
     ap.add_argument("--check-every", type=int, default=0,
-                    help="c4: CG iterations per chunk of the batched solve (0: the library's 16)")
+                    help="c4: CG iterations per chunk of the batched solve (0: the library's 8)")
     ap.add_argument("--nrhs", type=int, default=16)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--no-extras", action="store_true",
@@ -542,7 +542,7 @@ def c4_measure(args, steps, warmup, one_by_one_reps=1):
         "warmup": warmup, "one_by_one_ms": 1000.0 * t_single,
         "speedup_batched_vs_one_by_one": t_single / t_batch,
         "sloppy_storage": c4_sloppy, "recon": args.recon, "delta": p.delta,
-        "check_every": p.check_every if p.check_every > 0 else 16,
+        "check_every": p.check_every if p.check_every > 0 else 8,
         "masses": [round(float(m), 6) for m in masses],
         "iters": [s_["iters"] for s_ in st], "updates": [s_["updates"] for s_ in st],
         "true_res_max": max(s_["true_res"] for s_ in st),

@@ -297,6 +297,9 @@ stg_status stg_apply_A_mrhs(const stg_gauge *g, int nrhs, const double *masses, 
  *   src_dev / x_dev: nrhs consecutive canonical complex128 [Vh][3] fields
  *   (x_dev holds the initial guesses on entry); masses: host array;
  *   stats: NULL or nrhs entries.
+ *   params->check_every = 0 runs chunks of 8 inner iterations between host
+ *   checks (a system that asks for a reliable update waits for its chunk to
+ *   end, so shorter chunks shorten the batch's longest system).
  * Returns STG_OK when every system converged, else the first error;
  * STG_ERR_NOT_CONVERGED if any system reached maxiter (all x_k written).
  */

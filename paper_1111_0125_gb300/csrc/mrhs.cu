@@ -668,7 +668,10 @@ stg_status cg_solve_mrhs(stg_gauge *g, int n, const double *src, double *x, cons
     b->s = s;
     b->launches = 0;
     b->maxiter = p->maxiter > 0 ? p->maxiter : 10L * 3L * g->geom.Vh;
-    b->chunk = p->check_every > 0 ? (p->check_every > 256 ? 256 : p->check_every) : 16;
+    // chunks of 8 by default: a system that asks for a reliable update idles
+    // until its chunk ends (measured at 16 systems on 24^3x48: FP32 inner
+    // 402.4 / 399.5 / 397.5 ms at 16 / 8 / 4 iterations per chunk)
+    b->chunk = p->check_every > 0 ? (p->check_every > 256 ? 256 : p->check_every) : 8;
     b->pending.clear();
     const size_t canon = (size_t)g->geom.Vh * 6;
     std::vector<int> slot_of(n, -1);
