@@ -28,6 +28,7 @@ and `c5` (a served Poisson stream: saturation, then p50 / p99 at 0.7 of it).
   python bench.py --workload lgroup           # lattice group vs one by one
   python bench.py --workload e1               # Dslash on the paper's 28^3x96 lattice
   python bench.py --workload slabs            # t-slab decomposition, Table 1 breakdown
+  python bench.py --impl reference --workload oracle   # CPU oracle Dslash / A per config
   python bench.py --kernels-only --reps 3     # kernels alone (for ncu)
 """
 from __future__ import annotations
@@ -117,6 +118,8 @@ def parse():
                     help="c5: further offered loads (fractions of saturation) to report")
     ap.add_argument("--check-every", type=int, default=0,
                     help="c4: CG iterations per chunk of the batched solve (0: the library's 8)")
+    ap.add_argument("--oracle-configs", default="c1,c2,c4,c3,e1",
+                    help="oracle workload: the configurations' lattices to time (comma list)")
     ap.add_argument("--nrhs", type=int, default=16)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--no-extras", action="store_true",
@@ -1009,9 +1012,10 @@ ORACLE_LATTICES = [("c1", (4, 4, 4, 4), "haar", 0.0), ("c2", (16, 16, 16, 32), "
 
 
 def run_oracle(args):
-    """The FP64 oracle's Dslash and A (as they stand: plain C, OpenMP site
-    loop) on every configuration's lattice, on all host cores and on one
-    core: the median of repeated calls, each measurement about a second, with
+    """The reference arm's per-configuration timing (`--impl reference
+    --workload oracle`): the FP64 oracle's Dslash and A (as they stand: plain
+    C, OpenMP site loop) on every configuration's lattice, on all host cores
+    and on one core: the median of repeated calls, each measurement about a second, with
     the compulsory bytes per call (FP64 / 18-real: 1248 B per site for the
     half-pass, 2544 B for A) over that time.  Host cores only; no GPU."""
     import gen
@@ -1019,7 +1023,10 @@ def run_oracle(args):
     oracle.build()
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     rows = []
+    wanted = {c.strip() for c in args.oracle_configs.split(",") if c.strip()}
     for name, dims, kind, eps in ORACLE_LATTICES:
+        if name not in wanted:
+            continue
         U = gen.gauge_field(dims, kind, seed=0, eps=eps) if kind == "exp" else gen.gauge_field(dims, kind, seed=0)
         chi = gen.source(dims, seed=1)
         vh = chi.shape[0]
@@ -1043,7 +1050,8 @@ def run_oracle(args):
                     row[f"{op}_{label}_reps"] = reps
         rows.append(row)
         print(json.dumps({"oracle_row": row}), flush=True)
-    print(json.dumps({"workload": "oracle Dslash and A, FP64 / 18-real, host cores", "cores": cores,
+    print(json.dumps({"impl": "reference",
+                      "workload": "oracle Dslash and A, FP64 / 18-real, host cores", "cores": cores,
                       "kind": "oracle", "unit": "ms per call (median)", "data": "synthetic",
                       "rows": rows}), flush=True)
 
@@ -1051,6 +1059,9 @@ def run_oracle(args):
 def main():
     args = parse()
     if args.workload == "oracle":
+        # the oracle is the reference arm: its per-configuration timing runs there
+        if args.impl != "reference":
+            sys.exit("--workload oracle times the reference arm: use --impl reference --workload oracle")
         run_oracle(args)
         return
     dims = tuple(int(v) for v in args.lattice.split(","))

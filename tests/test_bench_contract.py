@@ -38,3 +38,26 @@ def test_reference_arm_json_line():
     # one complete solve of the workload, measured
     fs = d["full_solve"]
     assert fs["seconds"] > 0 and fs["iters"] > 0 and fs["true_res"] <= 1e-10
+
+
+def test_oracle_workload_json_line():
+    """The reference arm's `--workload oracle` times the CPU oracle's Dslash
+    and A (host cores only, no GPU) per configuration lattice; without
+    `--impl reference` the workload is refused."""
+    bench = os.path.join(ROOT, "bench.py")
+    r = subprocess.run([sys.executable, bench, "--workload", "oracle", "--oracle-configs", "c1"],
+                       capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode != 0 and "--impl reference" in r.stderr
+    r = subprocess.run([sys.executable, bench, "--impl", "reference", "--workload", "oracle",
+                        "--oracle-configs", "c1,c2"],
+                       capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    d = json.loads([ln for ln in r.stdout.splitlines() if ln.startswith("{")][-1])
+    assert d["impl"] == "reference" and d["kind"] == "oracle" and d["cores"] >= 1
+    assert [row["config"] for row in d["rows"]] == ["c1", "c2"]
+    for row in d["rows"]:
+        for op in ("dslash", "apply_A"):
+            for where in ("all_cores", "one_core"):
+                assert row[f"{op}_{where}_ms"] > 0 and row[f"{op}_{where}_gbs"] > 0
+    c2 = d["rows"][1]
+    assert c2["lattice"] == "16x16x16x32" and c2["vh"] == 16 * 16 * 16 * 32 // 2
